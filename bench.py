@@ -1,0 +1,342 @@
+"""Benchmark: FSR of a 1920x1080 quarter-sampled frame at K=100 on GB300.
+
+One step = one reconstruction of the whole frame (weighting, 32x32 DFT,
+K x {argmax, damped update, circular-shift residual update}, inverse and
+write-back) through the C-ABI entry point ``fsr_reconstruct`` on inputs
+already resident in device memory.  ``e2e`` times the host entry point
+``fsr_reconstruct_host`` with the host<->device copies inside.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+Under torchrun (N > 1) every rank reconstructs its own frames on its own GPU
+(independent replicas: blocks share no data, so there is no collective);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W, B, L, K_ITERS, RHO, GAMMA = 1080, 1920, 4, 14, 100, 0.7, 0.5
+IMG_SEED = 2
+METRIC = "megapixels/s and 1080p fps at K=100 within oracle tolerance; p50/p99 serving latency"
+SMEM_BYTES_PER_CLK_SM = 128          # shared-memory bandwidth per SM per clock
+FP32_LANES_PER_SM = 128              # FP32 FMA lanes per SM
+W_BYTES_PER_COMPONENT_ITER = 8       # complex FP32 W entry read per component per iteration
+FLOPS_PER_COMPONENT_ITER = 11        # objective 3 + complex multiply-subtract 8
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _init_pg(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _oracle_sample(img, mask, rows, threads):
+    """Oracle on the blocks of the given block rows; returns (targets, ids, seconds)."""
+    import oracle
+    nbx = -(-W // B)
+    ids = np.concatenate([np.arange(r * nbx, (r + 1) * nbx) for r in rows])
+    t0 = time.perf_counter()
+    res = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K_ITERS, rho=RHO, gamma=GAMMA,
+                                  block_ids=ids, threads=threads)
+    return res, ids, time.perf_counter() - t0
+
+
+def _calibrated_rows(img, mask, threads, target_s):
+    """Block rows spread over the frame, as many as fit in about target_s."""
+    nby = -(-H // B)
+    _, _, t1 = _oracle_sample(img, mask, [nby // 2], threads)
+    n = int(max(1, min(nby, target_s / max(t1, 1e-6))))
+    return sorted(set(np.linspace(0, nby - 1, n).round().astype(int).tolist()))
+
+
+def run_reference(args, rank, world):
+    dist = _init_pg(world)
+    if rank != 0:
+        _barrier(dist)
+        return
+    from paper_2202_13926_gb300 import synth
+    import oracle
+    oracle.build()
+    img, mask = synth.fhd_quarter_case(IMG_SEED)
+    threads = os.cpu_count() or 1
+    # each step is a bounded sample: the whole run stays within about two minutes
+    per_step = min(6.0, 120.0 / max(1, args.steps + args.warmup))
+    rows = _calibrated_rows(img, mask, threads, target_s=per_step)
+    mp_step = len(rows) * B * W / 1e6
+    for _ in range(args.warmup):
+        _oracle_sample(img, mask, rows[:1], threads)
+    times = []
+    for _ in range(args.steps):
+        _, _, t = _oracle_sample(img, mask, rows, threads)
+        times.append(t)
+    tot = sum(times)
+    value = args.steps * mp_step / tot
+    sample = f"{len(rows)} of {-(-H // B)} block rows of the 1920x1080 frame per step ({len(rows) * (W // B)} blocks)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(),
+        "cpu_baseline": {"value": value, "unit": "MP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "fps_equivalent": value / (H * W / 1e6),
+    }
+    print(json.dumps(line), flush=True)
+    _barrier(dist)
+
+
+def _config():
+    return {"workload": "fsr_1080p_quarter_sampling_K100",
+            "image": f"{W}x{H} float32, seeded 1/f^2 noise + edges (seed {IMG_SEED})",
+            "mask": "quarter sampling: one random pixel per 2x2 cell known",
+            "block": B, "border": L, "support": B + 2 * L, "iters": K_ITERS,
+            "rho": RHO, "gamma": GAMMA, "freq_weight": True,
+            "l2": "L2 flushed (256 MiB write) before every timed step; flush outside the kernel events"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = _dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import __graft_entry__
+    from paper_2202_13926_gb300 import fsr, synth
+
+    dist = _init_pg(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        __graft_entry__.build()
+    _barrier(dist)
+    fsr.load_library()
+
+    img, mask = synth.fhd_quarter_case(IMG_SEED)
+    d_img = torch.from_numpy(img).to(dev)
+    d_mask = torch.from_numpy(mask).to(dev)
+    d_out = torch.empty_like(d_img)
+    handle = fsr.Handle(local)
+    params = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, params, d_out, stream)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local, os.path.join("/tmp", f"fsr_clocks_{os.getpid()}.csv"))
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, params, d_out, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = _max_over_ranks(dist, sum(step_ms) / 1e3)
+    mp = H * W / 1e6
+    value = world * args.steps * mp / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # e2e through the host entry point (pinned host buffers, copies inside)
+    h_img = torch.from_numpy(img).pin_memory()
+    h_mask = torch.from_numpy(mask).pin_memory()
+    h_out = torch.empty_like(h_img).pin_memory()
+    for _ in range(2):
+        fsr.fsr_reconstruct_host(handle.ptr, h_img, h_mask, params, h_out, stream)
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        fsr.fsr_reconstruct_host(handle.ptr, h_img, h_mask, params, h_out, stream)
+    e2e_s = _max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = world * args.e2e_steps * mp / e2e_s
+
+    out = d_out.cpu().numpy()
+    assert np.array_equal(out, h_out.numpy()), "host entry point disagrees with the device one"
+
+    if rank != 0:
+        handle.close()
+        return
+
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nblocks = (-(-H // B)) * (-(-W // B))
+    comps = nblocks * K_ITERS * (B + 2 * L) ** 2
+    kern_s = statistics.mean(step_ms) / 1e3
+    smem_gbs = comps * W_BYTES_PER_COMPONENT_ITER / kern_s / 1e9
+    smem_peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9
+    flops = comps * FLOPS_PER_COMPONENT_ITER / kern_s / 1e12
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = {
+        "bound": "smem", "achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s",
+        "frac": smem_gbs / smem_peak, "traffic": None,
+        "peak_source": f"derived: {n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_max:.0f} MHz (max SM clock)",
+        "algorithmic": f"{W_BYTES_PER_COMPONENT_ITER} B of W per component per iteration, "
+                       f"{nblocks} blocks x {K_ITERS} iters x 1024 components per launch",
+        "fp32": {"achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / fp32_peak,
+                 "algorithmic": f"{FLOPS_PER_COMPONENT_ITER} flop per component per iteration"},
+        "kernel": "fsr_blocks_kernel<float,4,12>",
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(),
+        "fps": world * args.steps / total_s,
+        "wall_s_timed_region": t_wall,
+        "e2e": {"value": e2e_value, "unit": "MP/s", "fps": world * args.e2e_steps / e2e_s,
+                "h2d_bytes_per_step": int(img.nbytes + mask.nbytes),
+                "d2h_bytes_per_step": int(img.nbytes)},
+        "gpu_launches": args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+        "device": {"name": props.name, "sm_count": n_sm},
+    }
+
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        rows = _calibrated_rows(img, mask, threads, target_s=10.0)
+        res, ids, t = _oracle_sample(img, mask, rows, threads)
+        nbx = W // B
+        got = np.stack([out[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+        truth = np.stack([img[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+        ref = res["target"]
+        d = np.abs(got.astype(np.float64) - ref)
+
+        def psnr(x):
+            e = np.mean((np.asarray(x, np.float64) - truth) ** 2)
+            return 10 * np.log10(255.0 ** 2 / e)
+        frac = float(np.mean(d <= 0.5))
+        dpsnr = abs(psnr(got) - psnr(ref))
+        line["cpu_baseline"] = {
+            "value": len(ids) * B * B / 1e6 / t, "unit": "MP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(rows)} of {-(-H // B)} block rows of the frame ({len(ids)} blocks), FP64 C oracle, OpenMP over blocks"}
+        line["parity"] = {"frac_within_0.5": frac, "max_abs_diff": float(d.max()),
+                          "psnr_gpu_db": psnr(got), "psnr_oracle_db": psnr(ref),
+                          "dpsnr_db": dpsnr, "pass": bool(frac >= 0.999 and dpsnr <= 0.01),
+                          "blocks_checked": int(len(ids))}
+    print(json.dumps(line), flush=True)
+    handle.close()
+
+
+if __name__ == "__main__":
+    main()

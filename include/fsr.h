@@ -1,0 +1,126 @@
+/*
+ * fsr.h - C-ABI of the GB300 (sm_103a) Frequency Selective Reconstruction
+ * library (libfsr_gb300.so).
+ *
+ * Method: Regensky, Grosche, Seiler, Kaup, "Real-Time Frequency Selective
+ * Reconstruction through Register-Based Argmax Calculation", MMSP 2020.
+ * Every B x B target block of the image is reconstructed on its own
+ * S x S support, S = B + 2L (Sec. II; Sec. III-A, Eq. 13):
+ *   w = rho^dist on known pixels, 0 elsewhere            (Eq. 5)
+ *   R_w = F2{f~ w},  W = F2{w}                             (Eq. 7)
+ *   K times: (u,v) = argmax w_f |R_w|^2                    (Eqs. 8, 9)
+ *            p = R_w[u,v] / W[0,0]                          (Eq. 10)
+ *            G[u,v] += gamma p S^2                          (Eq. 11)
+ *            R_w[k,l] -= gamma p W[(k-u) mod S, (l-v) mod S] (Eqs. 12, 14, 15)
+ *   g = IDFT2(G); out = f on known pixels, Re g elsewhere (end of Sec. II)
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - forward DFT e^{-j2pi(km+ln)/S} unnormalised, inverse 1/S^2 e^{+j...};
+ *     k pairs with the row index m;
+ *   - argmax ties go to the lowest linear index k*S + l;
+ *   - the output at unknown pixels is Re g (the model is complex because
+ *     single components are updated);
+ *   - pixels outside the image are unknown; a block with no known pixel in
+ *     its support outputs 0 at its unknown pixels;
+ *   - the weight centre of the even support is (S-1)/2.
+ *
+ * All entry points return an int status (FSR_OK or an FSR_ERR_* code); the
+ * text of the last error of a handle is available from fsr_last_error().
+ * Device pointers are owned by the caller; the library owns only its handle
+ * and the workspace it allocates inside it.  Entry points that take a stream
+ * are asynchronous on that stream unless stated otherwise.
+ */
+#ifndef FSR_GB300_H
+#define FSR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define FSR_OK              0
+#define FSR_ERR_INVALID_ARG 1   /* a pointer, size or parameter is out of range */
+#define FSR_ERR_OOM         2   /* a device or pinned allocation failed / cap exceeded */
+#define FSR_ERR_CUDA        3   /* a CUDA runtime call or a kernel launch failed */
+#define FSR_ERR_TIMEOUT     4   /* a bounded device-side wait gave up */
+#define FSR_ERR_UNSUPPORTED 5   /* valid request this build does not implement */
+
+/* Arithmetic of the iteration (fsr_params.precision). */
+#define FSR_FP32       0  /* FP32 everywhere (the production path) */
+#define FSR_FP64_DEBUG 1  /* FP64 everywhere; selection sequences comparable with an FP64 reference */
+
+/* Library configuration (fsr_create). */
+typedef struct fsr_config {
+    int device;              /* CUDA device ordinal the handle is bound to */
+    size_t workspace_bytes;  /* cap on device memory the handle may allocate; 0 = no cap */
+} fsr_config;
+
+/* Method parameters (Sec. II; defaults of Sec. IV: B=4, rho=0.7, gamma=0.5). */
+typedef struct fsr_params {
+    int block;        /* B: target block size; one of 2, 4, 8, 16 */
+    int border;       /* L: border; S = B + 2L must equal 32 */
+    int iters;        /* K: number of iterations, 0 <= K <= 65535 */
+    float rho;        /* rho-hat of Eq. (5), in (0, 1] */
+    float gamma;      /* gamma of Eqs. (11)-(12), in (0, 1] */
+    int freq_weight;  /* 1: objective w_f |R_w|^2 (Eq. 8, paper default); 0: |R_w|^2 */
+    int precision;    /* FSR_FP32 or FSR_FP64_DEBUG */
+    int16_t *seq_out; /* optional DEVICE buffer of N*K entries (N = number of blocks,
+                         block b = by*ceil(width/B) + bx): the selected u*S+v of each
+                         iteration, -1 for a block without known pixels; NULL = off */
+} fsr_params;
+
+typedef struct fsr_handle fsr_handle;
+
+/* Create a handle on cfg->device.  Checks that the device runs this build
+ * (sm_103a) and sets the kernels' shared-memory limits.
+ * Errors: INVALID_ARG (NULL pointers, bad ordinal), UNSUPPORTED (other GPU),
+ * CUDA.  On error *out is set to NULL. */
+int fsr_create(const fsr_config *cfg, fsr_handle **out);
+
+/* Release the handle and every device/pinned buffer it owns.  Waits for
+ * nothing: the caller must not destroy a handle with work in flight.
+ * NULL is accepted and ignored. */
+int fsr_destroy(fsr_handle *h);
+
+/* Text of the last error recorded on h (never NULL; "" after success).
+ * With h == NULL: the last error of fsr_create in this thread. */
+const char *fsr_last_error(const fsr_handle *h);
+
+/* Reconstruct one single-channel image on the device (Sec. II, Sec. III-A).
+ *   img    DEVICE float32, height x width, row pitch `pitch` elements;
+ *          values at unknown pixels are never used (may be NaN)
+ *   mask   DEVICE uint8, same geometry and pitch; nonzero = known pixel
+ *   out    DEVICE float32, same geometry and pitch; every in-image pixel is
+ *          written: known pixels bit-exact copies of img, unknown ones Re g.
+ *          out must not overlap img or mask (supports read neighbour halos).
+ *   stream cudaStream_t (NULL = legacy default stream); the call only
+ *          enqueues work and returns.
+ * Errors: INVALID_ARG (NULL pointers, sizes <= 0, pitch < width, overlap,
+ * parameters out of range), UNSUPPORTED (S != 32, block not in {2,4,8,16}),
+ * CUDA (launch failure). */
+int fsr_reconstruct(fsr_handle *h, const float *img, const uint8_t *mask,
+                    int height, int width, int pitch, const fsr_params *p,
+                    float *out, void *stream);
+
+/* Same as fsr_reconstruct with HOST buffers (tightly packed when pitch ==
+ * width): copies img and mask to handle-owned device buffers, reconstructs,
+ * copies the result back into host `out` and synchronises `stream` before
+ * returning.  Pinned host memory gives full copy bandwidth; pageable memory
+ * works but is slower.  p->seq_out, if set, must still be a device buffer.
+ * Errors: as fsr_reconstruct, plus OOM when the device buffers cannot be
+ * allocated within the handle's workspace cap. */
+int fsr_reconstruct_host(fsr_handle *h, const float *img, const uint8_t *mask,
+                         int height, int width, int pitch, const fsr_params *p,
+                         float *out, void *stream);
+
+/* Number of target blocks N = ceil(height/B) * ceil(width/B) (Eq. 13);
+ * 0 for invalid sizes. */
+long long fsr_num_blocks(int height, int width, int block);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSR_GB300_H */

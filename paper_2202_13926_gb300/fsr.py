@@ -1,0 +1,217 @@
+"""ctypes binding of libfsr_gb300.so (declared in include/fsr.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of the library.  There is no CPU fallback: if the library is not
+built, or the device is not an sm_103a GPU, the calls raise.
+
+Tensors are torch tensors: device tensors for ``fsr_reconstruct`` (PyTorch
+owns the memory and the stream), host tensors or numpy arrays for
+``fsr_reconstruct_host``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+FSR_OK = 0
+FSR_ERR_INVALID_ARG = 1
+FSR_ERR_OOM = 2
+FSR_ERR_CUDA = 3
+FSR_ERR_TIMEOUT = 4
+FSR_ERR_UNSUPPORTED = 5
+
+FSR_FP32 = 0
+FSR_FP64_DEBUG = 1
+PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG}
+
+# every function declared in include/fsr.h
+EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
+            "fsr_reconstruct_host", "fsr_num_blocks")
+
+
+class FsrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[fsr status {code}] {msg}")
+        self.code = code
+
+
+class fsr_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class fsr_params(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("iters", ctypes.c_int),
+                ("rho", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("freq_weight", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seq_out", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"{p} is missing: build it with __graft_entry__.build() "
+                "(the CUDA library is required; there is no fallback)")
+        lib = ctypes.CDLL(p)
+        vp, ip = ctypes.c_void_p, ctypes.c_int
+        lib.fsr_create.argtypes = [ctypes.POINTER(fsr_config), ctypes.POINTER(vp)]
+        lib.fsr_create.restype = ip
+        lib.fsr_destroy.argtypes = [vp]
+        lib.fsr_destroy.restype = ip
+        lib.fsr_last_error.argtypes = [vp]
+        lib.fsr_last_error.restype = ctypes.c_char_p
+        for name in ("fsr_reconstruct", "fsr_reconstruct_host"):
+            f = getattr(lib, name)
+            f.argtypes = [vp, vp, vp, ip, ip, ip, ctypes.POINTER(fsr_params), vp, vp]
+            f.restype = ip
+        lib.fsr_num_blocks.argtypes = [ip, ip, ip]
+        lib.fsr_num_blocks.restype = ctypes.c_longlong
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(code: int, handle) -> None:
+    if code != FSR_OK:
+        lib = load_library()
+        msg = lib.fsr_last_error(handle).decode(errors="replace")
+        raise FsrError(code, msg)
+
+
+def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=True,
+                precision="fp32", seq_out=None) -> fsr_params:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    seq_ptr = None
+    if seq_out is not None:
+        import torch
+        if not (isinstance(seq_out, torch.Tensor) and seq_out.is_cuda and seq_out.dtype == torch.int16
+                and seq_out.is_contiguous()):
+            raise ValueError("seq_out must be a contiguous int16 CUDA tensor")
+        seq_ptr = seq_out.data_ptr()
+    return fsr_params(int(block), int(border), int(iters), float(rho), float(gamma),
+                      int(bool(freq_weight)), prec, seq_ptr)
+
+
+def fsr_num_blocks(height: int, width: int, block: int) -> int:
+    return int(load_library().fsr_num_blocks(int(height), int(width), int(block)))
+
+
+def fsr_last_error(handle=None) -> str:
+    return load_library().fsr_last_error(handle).decode(errors="replace")
+
+
+def fsr_create(device: int = 0, workspace_bytes: int = 0) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.fsr_create(ctypes.byref(fsr_config(int(device), int(workspace_bytes))),
+                          ctypes.byref(h)), None)
+    return h.value
+
+
+def fsr_destroy(handle) -> None:
+    load_library().fsr_destroy(handle)
+
+
+def _geometry(img, mask, out):
+    import torch
+    if img.dim() != 2 or mask.shape != img.shape or out.shape != img.shape:
+        raise ValueError("img, mask and out must be 2-D tensors of one shape")
+    if img.dtype != torch.float32 or out.dtype != torch.float32 or mask.dtype != torch.uint8:
+        raise ValueError("img/out must be float32 and mask uint8")
+    pitch = img.stride(0)
+    for t in (img, mask, out):
+        if t.stride(1) != 1 or t.stride(0) != pitch:
+            raise ValueError("img, mask and out must share one row pitch with unit column stride")
+    return img.shape[0], img.shape[1], pitch
+
+
+def fsr_reconstruct(handle, img, mask, params: fsr_params, out, stream=None) -> None:
+    """Enqueue the reconstruction of one image (device tensors) on ``stream``
+    (a torch.cuda.Stream, a raw cudaStream_t int, or None = current stream)."""
+    import torch
+    for t in (img, mask, out):
+        if not t.is_cuda:
+            raise ValueError("fsr_reconstruct takes CUDA tensors (use fsr_reconstruct_host for host data)")
+    H, W, pitch = _geometry(img, mask, out)
+    if stream is None:
+        stream = torch.cuda.current_stream(img.device).cuda_stream
+    elif isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
+    _check(load_library().fsr_reconstruct(handle, img.data_ptr(), mask.data_ptr(), H, W, pitch,
+                                          ctypes.byref(params), out.data_ptr(), stream), handle)
+
+
+def fsr_reconstruct_host(handle, img, mask, params: fsr_params, out, stream=None) -> None:
+    """Reconstruct host data (torch CPU tensors, ideally pinned, or numpy
+    arrays); copies in, computes and copies out inside the call."""
+    import numpy as np
+    import torch
+
+    def as_tensor(x):
+        return torch.from_numpy(x) if isinstance(x, np.ndarray) else x
+    img, mask, out = as_tensor(img), as_tensor(mask), as_tensor(out)
+    for t in (img, mask, out):
+        if t.is_cuda:
+            raise ValueError("fsr_reconstruct_host takes host tensors")
+    H, W, pitch = _geometry(img, mask, out)
+    if stream is None:
+        stream = 0
+    elif isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
+    _check(load_library().fsr_reconstruct_host(handle, img.data_ptr(), mask.data_ptr(), H, W, pitch,
+                                               ctypes.byref(params), out.data_ptr(), stream), handle)
+
+
+class Handle:
+    """Owning wrapper of an ``fsr_handle``."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.device = device
+        self.ptr = fsr_create(device, workspace_bytes)
+
+    def close(self):
+        if self.ptr:
+            fsr_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reconstruct(self, img, mask, out=None, stream=None, **kw):
+        import torch
+        if out is None:
+            out = torch.empty_like(img)
+        fsr_reconstruct(self.ptr, img, mask, make_params(**kw), out, stream)
+        return out
+
+    def reconstruct_host(self, img, mask, out=None, stream=None, **kw):
+        import numpy as np
+        if out is None:
+            out = np.empty(img.shape, np.float32)
+        fsr_reconstruct_host(self.ptr, img, mask, make_params(**kw), out, stream)
+        return out

@@ -1,0 +1,50 @@
+"""Shared helpers of the GPU parity tests: acceptance metrics and the
+tie-class rule for comparing selection sequences.
+
+Acceptance of the FP32 path against the FP64 oracle (written in the tests):
+  * |gpu - oracle| <= 0.5 grey levels on >= 99.9 % of the pixels,
+  * PSNR against the ground-truth image within 0.01 dB of the oracle's,
+  * known pixels bit-exact.
+FP64 debug path: identical selection sequences, except at a step where the
+oracle's relative gap between the best and second-best objective is below
+1e-12 ("tie class": the two choices are equal to rounding).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GREY_TOL = 0.5
+FRAC_MIN = 0.999
+PSNR_TOL_DB = 0.01
+TIE_MARGIN = 1e-12
+
+
+def psnr(x, truth, mask=None):
+    d = np.asarray(x, np.float64) - np.asarray(truth, np.float64)
+    if mask is not None:
+        d = d[mask]
+    mse = float(np.mean(d * d))
+    return float("inf") if mse == 0 else 10.0 * np.log10(255.0 ** 2 / mse)
+
+
+def frac_within(a, b, tol=GREY_TOL):
+    return float(np.mean(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) <= tol))
+
+
+def sequence_mismatches(seq_gpu, seq_ref, margin_ref):
+    """Blocks whose sequences differ at a step that is not a tie.
+
+    Returns (n_hard, n_tie): counts of blocks whose first differing step has
+    an oracle margin >= TIE_MARGIN (hard) or below it (tie class)."""
+    seq_gpu = np.asarray(seq_gpu).astype(np.int64)
+    seq_ref = np.asarray(seq_ref).astype(np.int64)
+    diff = seq_gpu != seq_ref
+    rows = np.nonzero(diff.any(axis=1))[0]
+    n_hard = n_tie = 0
+    for r in rows:
+        first = int(np.argmax(diff[r]))
+        if margin_ref[r, first] < TIE_MARGIN:
+            n_tie += 1
+        else:
+            n_hard += 1
+    return n_hard, n_tie

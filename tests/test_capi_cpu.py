@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every declared entry point (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_13926_gb300 import build as B
+from paper_2202_13926_gb300 import fsr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(fsr_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return fsr.load_library()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert declared, "no declarations found in include/"
+    assert declared == set(fsr.EXPORTED)
+    so = ctypes.CDLL(B.LIB)
+    for name in declared:
+        assert hasattr(so, name), name
+
+
+def test_num_blocks(lib):
+    assert fsr.fsr_num_blocks(1080, 1920, 4) == 270 * 480
+    assert fsr.fsr_num_blocks(128, 128, 4) == 1024
+    assert fsr.fsr_num_blocks(37, 53, 4) == 10 * 14
+    assert fsr.fsr_num_blocks(0, 5, 4) == 0
+    assert fsr.fsr_num_blocks(5, 5, 0) == 0
+
+
+def test_null_handle_is_rejected_on_host(lib):
+    p = fsr.make_params()
+    r = lib.fsr_reconstruct(None, 1, 1, 8, 8, 8, ctypes.byref(p), 1, None)
+    assert r == fsr.FSR_ERR_INVALID_ARG
+    assert "handle" in lib.fsr_last_error(None).decode()
+
+
+def test_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.fsr_create(None, ctypes.byref(h)) == fsr.FSR_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.fsr_create(ctypes.byref(fsr.fsr_config(0, 0)), None) == fsr.FSR_ERR_INVALID_ARG
+
+
+def test_destroy_null_is_noop(lib):
+    assert lib.fsr_destroy(None) == fsr.FSR_OK

@@ -1,0 +1,196 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances are stated in tests/parity.py."""
+import numpy as np
+import pytest
+
+import oracle
+import parity as PA
+from paper_2202_13926_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_13926_gb300 import fsr
+    h = fsr.Handle(0)
+    yield h
+    h.close()
+
+
+def run_gpu(h, img, mask, **kw):
+    dev = torch.device("cuda:0")
+    seq = kw.pop("seq", False)
+    B = kw.get("block", 4)
+    K = kw.get("iters", 100)
+    seq_t = None
+    if seq:
+        n = -(-img.shape[0] // B) * -(-img.shape[1] // B)
+        seq_t = torch.full((n * max(K, 1),), -7, dtype=torch.int16, device=dev)
+    out = h.reconstruct(torch.from_numpy(np.ascontiguousarray(img)).to(dev),
+                        torch.from_numpy(np.ascontiguousarray(mask)).to(dev),
+                        seq_out=seq_t, **kw)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    if seq:
+        return o, seq_t.cpu().numpy().reshape(-1, max(K, 1))[:, :K]
+    return o
+
+
+def run_oracle(img, mask, B=4, K=100, **kw):
+    L = (32 - B) // 2
+    r = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K, **kw)
+    return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B), r
+
+
+def test_small_case_fp32(handle):
+    img, mask = synth.small_case()
+    got = run_gpu(handle, img, mask, iters=100)
+    ref, _ = run_oracle(img, mask, K=100)
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    frac = PA.frac_within(got, ref)
+    assert frac >= PA.FRAC_MIN, frac
+    dpsnr = abs(PA.psnr(got, img) - PA.psnr(ref, img))
+    assert dpsnr <= PA.PSNR_TOL_DB, dpsnr
+
+
+def test_small_case_fp64_sequences(handle):
+    img, mask = synth.small_case()
+    got, seq = run_gpu(handle, img, mask, iters=100, precision="fp64", seq=True)
+    ref, r = run_oracle(img, mask, K=100)
+    n_hard, n_tie = PA.sequence_mismatches(seq, r["seq"], r["margin"])
+    assert n_hard == 0, (n_hard, n_tie)
+    assert n_tie <= 2
+    assert np.max(np.abs(got - ref)) <= 1e-3
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+
+
+@pytest.mark.parametrize("H,W,B,K", [
+    (1, 1, 4, 5), (3, 5, 4, 10), (37, 53, 4, 25), (4, 4, 4, 0), (33, 31, 4, 1),
+    (37, 53, 2, 20), (37, 53, 8, 20), (40, 36, 16, 20), (70, 9, 4, 40),
+])
+def test_ragged_sizes(handle, H, W, B, K):
+    img = synth.sinusoid_image(H, W, seed=H * 100 + W)
+    mask = synth.iid_mask(H, W, seed=H + W + B, missing=0.6)
+    for prec in ("fp32", "fp64"):
+        got, seq = run_gpu(handle, img, mask, block=B, border=(32 - B) // 2, iters=K,
+                           precision=prec, seq=True)
+        ref, r = run_oracle(img, mask, B=B, K=K)
+        assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+        if prec == "fp64":
+            n_hard, _ = PA.sequence_mismatches(seq, r["seq"], r["margin"])
+            assert n_hard == 0
+            assert np.max(np.abs(got - ref)) <= 1e-3
+        else:
+            # FP32 may leave the FP64 path at a near-tie: allow the 0.1 % share
+            # of the acceptance rule, and at least one pixel on tiny images
+            n_out = int(np.sum(np.abs(got - ref) > PA.GREY_TOL))
+            assert n_out <= max(1, int((1 - PA.FRAC_MIN) * got.size)), n_out
+
+
+def test_degenerate_masks(handle):
+    H, W = 45, 61
+    img = synth.sinusoid_image(H, W, seed=3)
+    # nothing known: every block is skipped, unknown output is 0, seq is -1
+    z = np.zeros((H, W), np.uint8)
+    got, seq = run_gpu(handle, img, z, iters=10, seq=True)
+    assert np.all(got == 0.0) and np.all(seq == -1)
+    # everything known: the image comes back unchanged
+    got = run_gpu(handle, img, np.ones((H, W), np.uint8), iters=10)
+    assert np.array_equal(got, img.astype(np.float64))
+    # one macroblock-loss mask with fully lost supports inside big holes
+    m = synth.macroblock_mask(H, W, seed=4, lost=0.5, mb=16)
+    got = run_gpu(handle, img, m, iters=30)
+    ref, _ = run_oracle(img, m, K=30)
+    assert PA.frac_within(got, ref) >= PA.FRAC_MIN
+
+
+def test_nan_at_unknown_pixels_is_ignored(handle):
+    img, mask = synth.small_case(seed=5)
+    a = run_gpu(handle, img, mask, iters=40)
+    bad = img.copy(); bad[mask == 0] = np.nan
+    b = run_gpu(handle, bad, mask, iters=40)
+    assert np.array_equal(a, b)
+
+
+def test_row_pitch_larger_than_width(handle):
+    from paper_2202_13926_gb300 import fsr
+    img, mask = synth.small_case(seed=6)
+    H, W = img.shape
+    P = W + 24
+    dev = torch.device("cuda:0")
+    bi = torch.full((H, P), -1.0, device=dev); bm = torch.zeros((H, P), dtype=torch.uint8, device=dev)
+    bo = torch.full((H, P), -5.0, device=dev)
+    bi[:, :W] = torch.from_numpy(img).to(dev); bm[:, :W] = torch.from_numpy(mask).to(dev)
+    fsr.fsr_reconstruct(handle.ptr, bi[:, :W], bm[:, :W], fsr.make_params(iters=30), bo[:, :W])
+    torch.cuda.synchronize()
+    dense = run_gpu(handle, img, mask, iters=30)
+    assert np.array_equal(bo[:, :W].cpu().numpy().astype(np.float64), dense)
+    assert torch.all(bo[:, W:] == -5.0)
+
+
+def test_deterministic(handle):
+    img, mask = synth.small_case(seed=9)
+    a = run_gpu(handle, img, mask, iters=60)
+    b = run_gpu(handle, img, mask, iters=60)
+    assert np.array_equal(a, b)
+
+
+def test_host_entry_matches_device(handle):
+    img, mask = synth.small_case(seed=10)
+    dev_out = run_gpu(handle, img, mask, iters=50)
+    out = np.empty_like(img)
+    host = handle.reconstruct_host(img, mask, out, iters=50)
+    assert np.array_equal(host.astype(np.float64), dev_out)
+
+
+def test_invalid_arguments_report_codes(handle):
+    from paper_2202_13926_gb300 import fsr
+    img, mask = synth.small_case()
+    dev = torch.device("cuda:0")
+    ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
+    cases = [dict(block=4, border=10), dict(block=6, border=13), dict(iters=-1),
+             dict(rho=0.0), dict(gamma=1.5), dict(precision=7)]
+    codes = [fsr.FSR_ERR_UNSUPPORTED, fsr.FSR_ERR_UNSUPPORTED, fsr.FSR_ERR_INVALID_ARG,
+             fsr.FSR_ERR_INVALID_ARG, fsr.FSR_ERR_INVALID_ARG, fsr.FSR_ERR_UNSUPPORTED]
+    for kw, code in zip(cases, codes):
+        with pytest.raises(fsr.FsrError) as e:
+            handle.reconstruct(ti, tm, **kw)
+        assert e.value.code == code, kw
+    with pytest.raises(fsr.FsrError) as e:   # out aliasing img
+        fsr.fsr_reconstruct(handle.ptr, ti, tm, fsr.make_params(), ti)
+    assert e.value.code == fsr.FSR_ERR_INVALID_ARG
+
+
+def _sample_blocks(H, W, B, n, seed):
+    nbx, nby = -(-W // B), -(-H // B)
+    rng = np.random.default_rng(seed)
+    edge = [0, nbx - 1, nbx * (nby - 1), nbx * nby - 1, nbx // 2, nbx * (nby // 2)]
+    ids = np.unique(np.concatenate([edge, rng.choice(nbx * nby, n, replace=False)]))
+    return ids
+
+
+def test_fhd_quarter_sampled_blocks(handle):
+    """1920 x 1080 quarter sampling at K = 100, in the bench's launch
+    configuration; the oracle recomputes a sample of blocks one by one."""
+    img, mask = synth.fhd_quarter_case()
+    H, W, B = 1080, 1920, 4
+    got, seq = run_gpu(handle, img, mask, iters=100, seq=True)
+    ids = _sample_blocks(H, W, B, 1500, 11)
+    r = oracle.fsr_image_blocks(img, mask, K=100, block_ids=ids)
+    nbx = W // B
+    g_t = np.stack([got[(b // nbx) * B:(b // nbx) * B + B, (b % nbx) * B:(b % nbx) * B + B] for b in ids])
+    t_t = np.stack([img[(b // nbx) * B:(b // nbx) * B + B, (b % nbx) * B:(b % nbx) * B + B] for b in ids])
+    frac = PA.frac_within(g_t, r["target"])
+    assert frac >= PA.FRAC_MIN, frac
+    dpsnr = abs(PA.psnr(g_t, t_t) - PA.psnr(r["target"], t_t))
+    assert dpsnr <= PA.PSNR_TOL_DB, dpsnr
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    same = float(np.mean(np.all(seq[ids] == r["seq"], axis=1)))
+    assert same >= 0.5, same   # FP32 may leave the FP64 path at near-ties
