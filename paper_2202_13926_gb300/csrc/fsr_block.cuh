@@ -213,6 +213,7 @@ fsr_blocks_kernel(const KernelArgs a) {
         const int xc = x0 + lane;
         const bool xin = (unsigned)xc < (unsigned)a.W;
         bool anyk = false;
+        unsigned fmax_bits = 0;   // bits of max |f| over known pixels (order-preserving)
 #pragma unroll
         for (int m = 0; m < S; ++m) {
             const int y = y0 + m;
@@ -227,7 +228,19 @@ fsr_blocks_kernel(const KernelArgs a) {
             zr[m] = kn ? T(fv) * w : T(0);   // select: unknown values never enter
             zi[m] = w;
             anyk |= kn;
+            const unsigned ab = __float_as_uint(fv) & 0x7fffffffu;
+            fmax_bits = (kn && ab > fmax_bits) ? ab : fmax_bits;
         }
+        // z = x + j alpha w with alpha = 2^e >= max|f|: both halves of z get the
+        // same magnitude, so W keeps full precision through the shared FFT; a
+        // power of two is undone exactly.
+        fmax_bits = __reduce_max_sync(FULL, fmax_bits);
+        unsigned aexp = (fmax_bits >> 23) + 1u;             // exponent field of 2^e
+        aexp = (fmax_bits >= 0x00800000u && fmax_bits < 0x7e000000u) ? aexp : 127u;
+        const T alpha = T(__uint_as_float(aexp << 23));
+        const T inv2alpha = T(__uint_as_float((253u - aexp) << 23));   // 1 / (2 alpha)
+#pragma unroll
+        for (int m = 0; m < S; ++m) zi[m] = zi[m] * alpha;
 
         // target pixels of this lane
         int pix_m[P], pix_n[P];
@@ -279,8 +292,8 @@ fsr_blocks_kernel(const KernelArgs a) {
                 }
                 const T ar = zr[l], ai = zi[l];
                 T2 w1;
-                w1.x = (ai + ci) * T(0.5);
-                w1.y = (cr - ar) * T(0.5);
+                w1.x = (ai + ci) * inv2alpha;
+                w1.y = (cr - ar) * inv2alpha;
                 zr[l] = (ar + cr) * T(0.5);
                 zi[l] = (ai - ci) * T(0.5);
                 wrow_out[l] = w1;
@@ -289,8 +302,8 @@ fsr_blocks_kernel(const KernelArgs a) {
                 if (l2 != l) {
                     const T br = zr[l2], bi = zi[l2];
                     T2 w2;
-                    w2.x = (bi + di) * T(0.5);
-                    w2.y = (dr - br) * T(0.5);
+                    w2.x = (bi + di) * inv2alpha;
+                    w2.y = (dr - br) * inv2alpha;
                     zr[l2] = (br + dr) * T(0.5);
                     zi[l2] = (bi - di) * T(0.5);
                     wrow_out[l2] = w2;
