@@ -65,6 +65,24 @@ def _max_over_ranks(dist, x: float) -> float:
     return float(t.item())
 
 
+def _profiled_traffic():
+    """DRAM bytes per launch of the top kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "fsr_blocks_kernel_fp32_1080p_K100.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        prof = json.load(fh)
+    m = hashlib.sha256()
+    for src in prof.get("kernel_sources", []):
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            m.update(fh.read())
+    if m.hexdigest() != prof.get("kernel_source_sha256"):
+        return None
+    return prof["dram_bytes_read"] + prof["dram_bytes_write"]
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -285,7 +303,9 @@ def main():
     fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     roofline = {
         "bound": "smem", "achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s",
-        "frac": smem_gbs / smem_peak, "traffic": None,
+        "frac": smem_gbs / smem_peak, "traffic": _profiled_traffic(),
+        "traffic_note": "DRAM bytes per launch from profiles/fsr_blocks_kernel_fp32_1080p_K100.json "
+                        "(inputs are L2 resident; null when the kernel changed since the capture)",
         "peak_source": f"derived: {n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_max:.0f} MHz (max SM clock)",
         "algorithmic": f"{W_BYTES_PER_COMPONENT_ITER} B of W per component per iteration, "
                        f"{nblocks} blocks x {K_ITERS} iters x 1024 components per launch",

@@ -4,10 +4,14 @@
 //   * lane n first holds column n of the support, then (after one transpose
 //     through shared memory) lane k holds row k of the spectrum: R_w[k][0..31]
 //     lives in 64 registers of lane k for the whole iteration;
-//   * the forward transform is one complex 32 x 32 DFT of z = x + j w
-//     (x = f~ w, the weighted signal of Eq. 7, and w of Eq. 5), done as two
-//     register-resident radix-2 FFT passes; R_w and W are separated with the
-//     conjugate-symmetry identities, which makes both exactly Hermitian;
+//   * the forward transform is one complex 32 x 32 DFT of z = x + j 2^e w
+//     (x = (f~ - mu) w, the weighted signal of Eq. 7 less its weighted mean
+//     mu, and w of Eq. 5), done as two register-resident radix-2 FFT passes;
+//     Q = F2{x} and W are separated with the conjugate-symmetry identities,
+//     which makes both exactly Hermitian.  R_w = mu W + Q exactly; while only
+//     the DC basis image is selected, R_w is kept as a W + Q with the scalar
+//     a absorbing every DC update (no rounding of the spectrum); at the first
+//     other selection a W is folded into Q (see the design doc for the numerics);
 //   * W is kept in shared memory with every row stored twice in a row
 //     (W[i][0..31] W[i][0..31]), so the circularly shifted row
 //     W[(k-u) mod S][(l-v) mod S], l = 0..31 of Eqs. (12), (14), (15) is 32
@@ -30,7 +34,6 @@
 namespace fsrk {
 
 constexpr int S = 32;                 // support size of this kernel family
-constexpr int WSTRIDE = 2 * S + 1;    // doubled W row + 1 pad (bank spread)
 constexpr int TSTRIDE = S + 1;        // transpose buffer row stride
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -133,6 +136,12 @@ __device__ __forceinline__ void fft32(T (&re)[32], T (&im)[32]) {
     }
 }
 
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 __device__ __forceinline__ float warp_max(float x) {
     // objective values are >= +0, so their bit patterns order like the values
     return __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(x)));
@@ -143,22 +152,423 @@ __device__ __forceinline__ double warp_max(double x) {
     return x;
 }
 
+// Row stride (in complex elements) of the doubled W rows: 64 entries + pad,
+// chosen so that 32 lanes reading 32 different rows at one column hit
+// distinct banks (128-bit loads for FP32, 128-bit elements for FP64).
+template <typename T> struct WRow;
+template <> struct WRow<float> { static constexpr int stride = 2 * S + 2; };   // 528 B
+template <> struct WRow<double> { static constexpr int stride = 2 * S + 1; };  // 1040 B
+
 template <typename T>
 struct SmemLayout {
     using T2 = typename Vec2<T>::type;
+    static constexpr int WS = WRow<T>::stride;
     // CTA-shared tables
     static constexpr size_t w0_off = 0;                                 // S*S T
     static constexpr size_t wf_off = w0_off + sizeof(T) * S * S;        // S*S T
     static constexpr size_t cs_off = wf_off + sizeof(T) * S * S;        // S T2
     static constexpr size_t warp0_off = cs_off + sizeof(T2) * S;
     // per warp: doubled W rows, then the published row
-    static constexpr size_t w_elems = (size_t)S * WSTRIDE;
+    static constexpr size_t w_elems = (size_t)S * WS;
     static constexpr size_t per_warp = sizeof(T2) * (w_elems + S);
     static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
 };
 
 // Number of target pixels each lane accumulates for a B x B target.
 template <int B> struct TargetPix { static constexpr int P = (B * B + 31) / 32; };
+
+// Per-block values shared by the phases.
+template <typename T>
+struct BlockState {
+    T W0;   // W[0][0] = sum of w
+    T mu;   // weighted mean of the known values: R_w = mu W + Q at the start
+};
+
+// a1-a3: load the support (lane n = column n), weight it, transform it.
+// On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
+// row k in zr/zi and every row of W is in Wd twice in a row.
+template <typename T, int WS>
+__device__ __forceinline__ bool prepare_block(const KernelArgs& a, int y0, int x0, int lane,
+                                              const T* __restrict__ sw0,
+                                              typename Vec2<T>::type* Wd,
+                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
+    using T2 = typename Vec2<T>::type;
+    const int xc = x0 + lane;
+    const bool xin = (unsigned)xc < (unsigned)a.W;
+    unsigned known = 0;   // bit m: pixel (m, lane) is known
+    T sw = T(0), sfw = T(0);
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        const int y = y0 + m;
+        bool kn = false;
+        float fv = 0.f;
+        if (xin && (unsigned)y < (unsigned)a.H) {
+            const size_t off = (size_t)y * a.pitch + xc;
+            kn = __ldg(a.mask + off) != 0;
+            fv = __ldg(a.img + off);
+        }
+        zr[m] = kn ? T(fv) : T(0);   // select: unknown values never enter arithmetic
+        known |= kn ? (1u << m) : 0u;
+        const T w = kn ? sw0[m * S + lane] : T(0);
+        sw += w;
+        sfw += w * zr[m];
+    }
+    if (__ballot_sync(FULL, known != 0) == 0) return false;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(FULL, sw, o);
+        sfw += __shfl_xor_sync(FULL, sfw, o);
+    }
+    const T mu = sfw / sw;   // any value works; the weighted mean makes Q[0][0] ~ 0
+    st.mu = mu;
+
+    // x = (f - mu) w on known pixels; alpha = 2^e >= max|f - mu| so that both
+    // halves of z = x + j alpha w have one magnitude (W keeps FP32 precision
+    // through the shared FFT); powers of two are undone exactly.
+    unsigned dmax = 0;
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        const bool kn = (known >> m) & 1u;
+        const T w = kn ? sw0[m * S + lane] : T(0);
+        const T d = zr[m] - mu;
+        zr[m] = kn ? d * w : T(0);
+        zi[m] = w;
+        const unsigned ab = __float_as_uint((float)d) & 0x7fffffffu;
+        dmax = (kn && ab > dmax) ? ab : dmax;
+    }
+    dmax = __reduce_max_sync(FULL, dmax);
+    unsigned aexp = (dmax >> 23) + 1u;             // exponent field of 2^e
+    aexp = (dmax >= 0x00800000u && dmax < 0x7e000000u) ? aexp : 127u;
+    const T alpha = T(__uint_as_float(aexp << 23));
+    const T inv2alpha = T(__uint_as_float((253u - aexp) << 23));   // 1 / (2 alpha)
+#pragma unroll
+    for (int m = 0; m < S; ++m) zi[m] = zi[m] * alpha;
+
+    // a3: FFT over m (lane n holds column n)
+    fft32<T>(zr, zi);
+    // transpose through this warp's (not yet used) W area
+    T2* tb = Wd;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        T2 v; v.x = zr[k]; v.y = zi[k];
+        tb[k * TSTRIDE + lane] = v;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int n = 0; n < S; ++n) {
+        const T2 v = tb[lane * TSTRIDE + n];
+        zr[n] = v.x; zi[n] = v.y;
+    }
+    __syncwarp();
+    // FFT over n: lane k holds Z[k][0..31]
+    fft32<T>(zr, zi);
+
+    // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,  W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha)
+    const int src = (S - lane) & (S - 1);
+    T2* wrow_out = Wd + lane * WS;
+    T W0 = T(0);
+#pragma unroll
+    for (int l = 0; l <= S / 2; ++l) {
+        const int l2 = (S - l) & (S - 1);
+        const T cr = __shfl_sync(FULL, zr[l2], src);
+        const T ci = __shfl_sync(FULL, zi[l2], src);
+        T dr = cr, di = ci;
+        if (l2 != l) {
+            dr = __shfl_sync(FULL, zr[l], src);
+            di = __shfl_sync(FULL, zi[l], src);
+        }
+        const T ar = zr[l], ai = zi[l];
+        T2 w1;
+        w1.x = (ai + ci) * inv2alpha;
+        w1.y = (cr - ar) * inv2alpha;
+        zr[l] = (ar + cr) * T(0.5);
+        zi[l] = (ai - ci) * T(0.5);
+        wrow_out[l] = w1;
+        wrow_out[l + S] = w1;
+        if (l == 0) W0 = w1.x;
+        if (l2 != l) {
+            const T br = zr[l2], bi = zi[l2];
+            T2 w2;
+            w2.x = (bi + di) * inv2alpha;
+            w2.y = (dr - br) * inv2alpha;
+            zr[l2] = (br + dr) * T(0.5);
+            zi[l2] = (bi - di) * T(0.5);
+            wrow_out[l2] = w2;
+            wrow_out[l2 + S] = w2;
+        }
+    }
+    st.W0 = __shfl_sync(FULL, W0, 0);
+    __syncwarp();
+    return true;
+}
+
+// R = a W + Q for one component (the DC-split representation); the same
+// rounded operations everywhere, so every copy of a value is bit-identical.
+template <typename T>
+__device__ __forceinline__ void split_value(T ar, T ai, T wr, T wi, T qr, T qi, T& rr, T& ri) {
+    rr = fma_rn(ar, wr, fma_rn(-ai, wi, qr));
+    ri = fma_rn(ar, wi, fma_rn(ai, wr, qi));
+}
+
+// Eq. (12) for one component: R -= c W.
+template <typename T>
+__device__ __forceinline__ void residual_update(T& re, T& im, T wr, T wi, T cr, T ci) {
+    re = fma_rn(-cr, wr, fma_rn(ci, wi, re));
+    im = fma_rn(-cr, wi, fma_rn(-ci, wr, im));
+}
+
+// ---------------------------------------------------------------- FP32 loop
+// Lane k holds Q[k][l] in zr[l], zi[l] and w_f[k][l] in wfr[min(l, 32-l)].
+// Every pass leaves in g[j] the maximum of the objective over the group of
+// four components 4j..4j+3 of the lane's row (short, independent max chains);
+// the argmax then needs only the one group that holds the block maximum.
+
+constexpr int WS32 = WRow<float>::stride;
+constexpr int NG = 8;            // groups of four components per row
+
+__device__ __forceinline__ float wf_at(const float (&wfr)[S / 2 + 1], int l) {
+    return wfr[l <= S / 2 ? l : S - l];
+}
+
+__device__ __forceinline__ void group_max(float (&g)[NG], int i, float o0, float o1) {
+    // pair i = components 2i, 2i+1 belongs to group i / 2
+    if ((i & 1) == 0) g[i >> 1] = fmaxf(o0, o1);
+    else g[i >> 1] = max3(g[i >> 1], o0, o1);
+}
+
+// objective pass of R = a W + Q over the unshifted row k (DC phase)
+__device__ __forceinline__ void pass_split_objective(const float (&zr)[S], const float (&zi)[S],
+                                                     const float (&wfr)[S / 2 + 1], const float2* wrow,
+                                                     float ar, float ai, float (&g)[NG]) {
+    const float4* p = reinterpret_cast<const float4*>(wrow);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) {
+        const float4 w = p[i];
+        float r0r, r0i, r1r, r1i;
+        split_value(ar, ai, w.x, w.y, zr[2 * i], zi[2 * i], r0r, r0i);
+        split_value(ar, ai, w.z, w.w, zr[2 * i + 1], zi[2 * i + 1], r1r, r1i);
+        group_max(g, i, objective<float>(r0r, r0i, wf_at(wfr, 2 * i)),
+                  objective<float>(r1r, r1i, wf_at(wfr, 2 * i + 1)));
+    }
+}
+
+// fold a W into Q (end of the DC phase)
+__device__ __forceinline__ void pass_fold(float (&zr)[S], float (&zi)[S], const float2* wrow,
+                                          float ar, float ai) {
+    const float4* p = reinterpret_cast<const float4*>(wrow);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) {
+        const float4 w = p[i];
+        split_value(ar, ai, w.x, w.y, zr[2 * i], zi[2 * i], zr[2 * i], zi[2 * i]);
+        split_value(ar, ai, w.z, w.w, zr[2 * i + 1], zi[2 * i + 1], zr[2 * i + 1], zi[2 * i + 1]);
+    }
+}
+
+// Eq. (12) with the shifted row W[(k-u)][(l-v) mod 32], then the objective.
+// base points at entry (32-v) mod 32 of the doubled row k-u, so entry l of
+// the shifted row is base[l]; for odd offsets the 16-byte loads start one
+// entry earlier and each component takes the upper half of one load and the
+// lower half of the next.
+template <bool ODD>
+__device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
+                                            const float2* base, float cr, float ci, float (&g)[NG]) {
+    const float4* p = reinterpret_cast<const float4*>(ODD ? base - 1 : base);
+    float4 prev = ODD ? p[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) {
+        float w0r, w0i, w1r, w1i;
+        if (ODD) {
+            const float4 next = p[i + 1];
+            w0r = prev.z; w0i = prev.w; w1r = next.x; w1i = next.y;
+            prev = next;
+        } else {
+            const float4 w = p[i];
+            w0r = w.x; w0i = w.y; w1r = w.z; w1i = w.w;
+        }
+        residual_update(zr[2 * i], zi[2 * i], w0r, w0i, cr, ci);
+        residual_update(zr[2 * i + 1], zi[2 * i + 1], w1r, w1i, cr, ci);
+        group_max(g, i, objective<float>(zr[2 * i], zi[2 * i], wf_at(wfr, 2 * i)),
+                  objective<float>(zr[2 * i + 1], zi[2 * i + 1], wf_at(wfr, 2 * i + 1)));
+    }
+}
+
+// Lane u writes components 4j..4j+3 of its row to rowbuf[0..3] (j uniform).
+__device__ __forceinline__ void publish_group(const float (&zr)[S], const float (&zi)[S], int j,
+                                              bool mine, float2* rowbuf) {
+    float4* pub = reinterpret_cast<float4*>(rowbuf);
+    switch (j) {
+#define FSR_PUB_CASE(J)                                                                      \
+        case J:                                                                              \
+            if (mine) {                                                                      \
+                pub[0] = make_float4(zr[4 * J], zi[4 * J], zr[4 * J + 1], zi[4 * J + 1]);     \
+                pub[1] = make_float4(zr[4 * J + 2], zi[4 * J + 2], zr[4 * J + 3], zi[4 * J + 3]); \
+            }                                                                                \
+            break;
+        FSR_PUB_CASE(0) FSR_PUB_CASE(1) FSR_PUB_CASE(2) FSR_PUB_CASE(3)
+        FSR_PUB_CASE(4) FSR_PUB_CASE(5) FSR_PUB_CASE(6) FSR_PUB_CASE(7)
+#undef FSR_PUB_CASE
+        default: break;
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* Wd, float2* rowbuf,
+                                        const float* __restrict__ swf, const float2* __restrict__ scs,
+                                        const BlockState<float>& st, float gamma, int K, int L, int lane,
+                                        int16_t* seq, float (&gacc)[TargetPix<B>::P]) {
+    constexpr int P = TargetPix<B>::P;
+    float wfr[S / 2 + 1];
+#pragma unroll
+    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
+    int pm[P], pn[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        pm[q] = L + (lane + 32 * q) / B;
+        pn[q] = L + (lane + 32 * q) % B;
+    }
+    const float invW0 = 1.f / st.W0;
+    const float2* wrow_k = Wd + lane * WS32;
+    float ar = st.mu, ai = 0.f;
+    bool split = true;   // R = a W + Q until the first non-DC selection
+    float g[NG];
+    pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
+
+    for (int nu = 0; nu < K; ++nu) {
+        // ---- a5: argmax with the lowest linear index on ties ----
+        const float m = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]), fmaxf(g[6], g[7]));
+        const unsigned Mb = __reduce_max_sync(FULL, __float_as_uint(m));
+        const int u = __ffs(__ballot_sync(FULL, __float_as_uint(m) == Mb)) - 1;
+        // first group of this lane's row that holds the maximum (used from lane u)
+        int jg = NG - 1;
+#pragma unroll
+        for (int j = NG - 2; j >= 0; --j) jg = (__float_as_uint(g[j]) == Mb) ? j : jg;
+        jg = __shfl_sync(FULL, jg, u);
+        publish_group(zr, zi, jg, lane == u, rowbuf);
+        __syncwarp();
+        const int cl = 4 * jg + (lane & 3);      // column examined by this lane
+        const float2 q = rowbuf[lane & 3];
+        float rr = q.x, ri = q.y;
+        if (split) {
+            const float2 w = Wd[u * WS32 + cl];
+            split_value(ar, ai, w.x, w.y, q.x, q.y, rr, ri);
+        }
+        const float o = objective<float>(rr, ri, swf[u * S + cl]);
+        const int vl = __ffs(__ballot_sync(FULL, __float_as_uint(o) == Mb)) - 1;   // lanes 0..3 lead
+        const int v = 4 * jg + vl;
+        const float Rr = __shfl_sync(FULL, rr, vl);
+        const float Ri = __shfl_sync(FULL, ri, vl);
+        __syncwarp();
+
+        // ---- a6: c = gamma p, p = R[u,v] / W[0,0] (Eqs. 10-11) ----
+        const float cr = gamma * (Rr * invW0);
+        const float ci = gamma * (Ri * invW0);
+        if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * S + v);
+#pragma unroll
+        for (int q2 = 0; q2 < P; ++q2) {
+            const float2 cs = scs[(u * pm[q2] + v * pn[q2]) & (S - 1)];
+            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+        }
+
+        // ---- a7: residual update (or DC bookkeeping), next objective ----
+        if (split) {
+            if ((u | v) == 0) {
+                ar -= cr;
+                ai -= ci;
+                pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
+                continue;
+            }
+            pass_fold(zr, zi, wrow_k, ar, ai);
+            split = false;
+        }
+        const int s = (S - v) & (S - 1);
+        const float2* base = Wd + ((lane - u) & (S - 1)) * WS32 + s;
+        if (s & 1) pass_update<true>(zr, zi, wfr, base, cr, ci, g);
+        else pass_update<false>(zr, zi, wfr, base, cr, ci, g);
+    }
+}
+
+// ---------------------------------------------------------------- FP64 loop
+// The debug arithmetic: plain scalar loop with the same representation and
+// selection rule, IEEE division for p.
+template <int B>
+__device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double2* Wd, double2* rowbuf,
+                                        const double* __restrict__ swf, const double2* __restrict__ scs,
+                                        const BlockState<double>& st, double gamma, int K, int L, int lane,
+                                        int16_t* seq, double (&gacc)[TargetPix<B>::P]) {
+    constexpr int P = TargetPix<B>::P;
+    constexpr int WS = WRow<double>::stride;
+    double wfr[S / 2 + 1];
+#pragma unroll
+    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
+    int pm[P], pn[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        pm[q] = L + (lane + 32 * q) / B;
+        pn[q] = L + (lane + 32 * q) % B;
+    }
+    const double2* wrow_k = Wd + lane * WS;
+    double ar = st.mu, ai = 0.0;
+    bool split = true;
+    double m = 0.0;
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+        double rr, ri;
+        split_value(ar, ai, wrow_k[l].x, wrow_k[l].y, zr[l], zi[l], rr, ri);
+        m = fmax(m, objective<double>(rr, ri, wfr[l <= S / 2 ? l : S - l]));
+    }
+    for (int nu = 0; nu < K; ++nu) {
+        const double M = warp_max(m);
+        const int u = __ffs(__ballot_sync(FULL, m == M)) - 1;
+        if (lane == u) {
+#pragma unroll
+            for (int l = 0; l < S; ++l) { double2 t; t.x = zr[l]; t.y = zi[l]; rowbuf[l] = t; }
+        }
+        __syncwarp();
+        const double2 q = rowbuf[lane];
+        double rr = q.x, ri = q.y;
+        if (split) split_value(ar, ai, Wd[u * WS + lane].x, Wd[u * WS + lane].y, q.x, q.y, rr, ri);
+        const double o = objective<double>(rr, ri, swf[u * S + lane]);
+        const int v = __ffs(__ballot_sync(FULL, o == M)) - 1;
+        const double Rr = __shfl_sync(FULL, rr, v);
+        const double Ri = __shfl_sync(FULL, ri, v);
+        __syncwarp();
+        const double cr = gamma * (Rr / st.W0);
+        const double ci = gamma * (Ri / st.W0);
+        if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * S + v);
+#pragma unroll
+        for (int q2 = 0; q2 < P; ++q2) {
+            const double2 cs = scs[(u * pm[q2] + v * pn[q2]) & (S - 1)];
+            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+        }
+        if (split) {
+            if ((u | v) == 0) {
+                ar -= cr;
+                ai -= ci;
+                m = 0.0;
+#pragma unroll
+                for (int l = 0; l < S; ++l) {
+                    double r1, r2;
+                    split_value(ar, ai, wrow_k[l].x, wrow_k[l].y, zr[l], zi[l], r1, r2);
+                    m = fmax(m, objective<double>(r1, r2, wfr[l <= S / 2 ? l : S - l]));
+                }
+                continue;
+            }
+#pragma unroll
+            for (int l = 0; l < S; ++l)
+                split_value(ar, ai, wrow_k[l].x, wrow_k[l].y, zr[l], zi[l], zr[l], zi[l]);
+            split = false;
+        }
+        const double2* wrow = Wd + ((lane - u) & (S - 1)) * WS + ((S - v) & (S - 1));
+        m = 0.0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            const double2 w = wrow[l];
+            residual_update(zr[l], zi[l], w.x, w.y, cr, ci);
+            m = fmax(m, objective<double>(zr[l], zi[l], wfr[l <= S / 2 ? l : S - l]));
+        }
+    }
+}
 
 template <typename T, int B, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1)
@@ -208,164 +618,17 @@ fsr_blocks_kernel(const KernelArgs a) {
         const int bx = (int)(blk - (long long)by * a.nbx);
         const int y0 = by * B - L, x0 = bx * B - L;
 
-        // ---- a1/a2: load the support column of this lane and weight it ----
         T zr[S], zi[S];
-        const int xc = x0 + lane;
-        const bool xin = (unsigned)xc < (unsigned)a.W;
-        bool anyk = false;
-        unsigned fmax_bits = 0;   // bits of max |f| over known pixels (order-preserving)
-#pragma unroll
-        for (int m = 0; m < S; ++m) {
-            const int y = y0 + m;
-            bool kn = false;
-            float fv = 0.f;
-            if (xin && (unsigned)y < (unsigned)a.H) {
-                const size_t off = (size_t)y * a.pitch + xc;
-                kn = __ldg(a.mask + off) != 0;
-                fv = __ldg(a.img + off);
-            }
-            const T w = kn ? sw0[m * S + lane] : T(0);
-            zr[m] = kn ? T(fv) * w : T(0);   // select: unknown values never enter
-            zi[m] = w;
-            anyk |= kn;
-            const unsigned ab = __float_as_uint(fv) & 0x7fffffffu;
-            fmax_bits = (kn && ab > fmax_bits) ? ab : fmax_bits;
-        }
-        // z = x + j alpha w with alpha = 2^e >= max|f|: both halves of z get the
-        // same magnitude, so W keeps full precision through the shared FFT; a
-        // power of two is undone exactly.
-        fmax_bits = __reduce_max_sync(FULL, fmax_bits);
-        unsigned aexp = (fmax_bits >> 23) + 1u;             // exponent field of 2^e
-        aexp = (fmax_bits >= 0x00800000u && fmax_bits < 0x7e000000u) ? aexp : 127u;
-        const T alpha = T(__uint_as_float(aexp << 23));
-        const T inv2alpha = T(__uint_as_float((253u - aexp) << 23));   // 1 / (2 alpha)
-#pragma unroll
-        for (int m = 0; m < S; ++m) zi[m] = zi[m] * alpha;
-
-        // target pixels of this lane
-        int pix_m[P], pix_n[P];
+        BlockState<T> st;
         T gacc[P];
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const int pidx = lane + 32 * q;
-            pix_m[q] = L + pidx / B;
-            pix_n[q] = L + pidx % B;
-            gacc[q] = T(0);
-        }
+        for (int q = 0; q < P; ++q) gacc[q] = T(0);
 
-        if (__any_sync(FULL, anyk)) {
-            // ---- a3: z = x + j w, FFT over m (columns) ----
-            fft32<T>(zr, zi);
-            // transpose through the (not yet used) W area of this warp
-            T2* tb = Wd;
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < S; ++k) {
-                T2 v; v.x = zr[k]; v.y = zi[k];
-                tb[k * TSTRIDE + lane] = v;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int n = 0; n < S; ++n) {
-                const T2 v = tb[lane * TSTRIDE + n];
-                zr[n] = v.x; zi[n] = v.y;
-            }
-            __syncwarp();
-            // FFT over n (rows): lane k now holds Z[k][0..31]
-            fft32<T>(zr, zi);
-
-            // Separate R_w = F2{x} and W = F2{w}:
-            //   R[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,
-            //   W[k][l] = (Z[k][l] - conj Z[-k][-l]) / 2j.
-            const int src = (S - lane) & (S - 1);
-            T2* wrow_out = Wd + lane * WSTRIDE;
-            T W0 = T(0);
-#pragma unroll
-            for (int l = 0; l <= S / 2; ++l) {
-                const int l2 = (S - l) & (S - 1);
-                const T cr = __shfl_sync(FULL, zr[l2], src);
-                const T ci = __shfl_sync(FULL, zi[l2], src);
-                T dr = cr, di = ci;
-                if (l2 != l) {
-                    dr = __shfl_sync(FULL, zr[l], src);
-                    di = __shfl_sync(FULL, zi[l], src);
-                }
-                const T ar = zr[l], ai = zi[l];
-                T2 w1;
-                w1.x = (ai + ci) * inv2alpha;
-                w1.y = (cr - ar) * inv2alpha;
-                zr[l] = (ar + cr) * T(0.5);
-                zi[l] = (ai - ci) * T(0.5);
-                wrow_out[l] = w1;
-                wrow_out[l + S] = w1;
-                if (l == 0) W0 = w1.x;
-                if (l2 != l) {
-                    const T br = zr[l2], bi = zi[l2];
-                    T2 w2;
-                    w2.x = (bi + di) * inv2alpha;
-                    w2.y = (dr - br) * inv2alpha;
-                    zr[l2] = (br + dr) * T(0.5);
-                    zi[l2] = (bi - di) * T(0.5);
-                    wrow_out[l2] = w2;
-                    wrow_out[l2 + S] = w2;
-                }
-            }
-            W0 = __shfl_sync(FULL, W0, 0);   // W[0][0] = sum of w
-
-            // frequency weights of this lane's row (w_f[k][l] = w_f[k][S-l])
-            T wfr[S / 2 + 1];
-#pragma unroll
-            for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
-
-            T rowmax = T(0);
-#pragma unroll
-            for (int l = 0; l < S; ++l)
-                rowmax = fmax(rowmax, objective<T>(zr[l], zi[l], wfr[l <= S / 2 ? l : S - l]));
-            __syncwarp();
-
-            int16_t* seq = a.seq ? a.seq + (size_t)blk * a.K : nullptr;
-            for (int nu = 0; nu < a.K; ++nu) {
-                // ---- a5: argmax, lowest linear index on ties ----
-                const T M = warp_max(rowmax);
-                const unsigned cand = __ballot_sync(FULL, rowmax == M);
-                const int u = __ffs(cand) - 1;
-                if (lane == u) {
-#pragma unroll
-                    for (int l = 0; l < S; ++l) { T2 v; v.x = zr[l]; v.y = zi[l]; rowbuf[l] = v; }
-                }
-                __syncwarp();
-                const T2 mine = rowbuf[lane];
-                const T o = objective<T>(mine.x, mine.y, swf[u * S + lane]);
-                const unsigned vb = __ballot_sync(FULL, o == M);
-                const int v = __ffs(vb) - 1;
-                const T2 Ruv = rowbuf[v];
-                __syncwarp();
-
-                // ---- a6: p = R[u,v] / W[0,0]; gamma p enters G (Eq. 11) ----
-                const T cr = gamma * (Ruv.x / W0);
-                const T ci = gamma * (Ruv.y / W0);
-                if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * S + v);
-#pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    const int t = (u * pix_m[q] + v * pix_n[q]) & (S - 1);
-                    const T2 cs = scs[t];
-                    gacc[q] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q]));
-                }
-
-                // ---- a7: R[k,l] -= gamma p W[k-u, l-v], then next objective ----
-                const T2* wrow = Wd + ((lane - u) & (S - 1)) * WSTRIDE + ((S - v) & (S - 1));
-                rowmax = T(0);
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    const T2 w = wrow[l];
-                    zr[l] = fma_rn(-cr, w.x, fma_rn(ci, w.y, zr[l]));
-                    zi[l] = fma_rn(-cr, w.y, fma_rn(-ci, w.x, zi[l]));
-                    rowmax = fmax(rowmax, objective<T>(zr[l], zi[l], wfr[l <= S / 2 ? l : S - l]));
-                }
-            }
+        int16_t* seq = a.seq ? a.seq + (size_t)blk * a.K : nullptr;
+        if (prepare_block<T, Lay::WS>(a, y0, x0, lane, sw0, Wd, zr, zi, st)) {
+            iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, a.K, L, lane, seq, gacc);
             __syncwarp();   // W area free for the next block
-        } else if (a.seq != nullptr && lane == 0) {
-            int16_t* seq = a.seq + (size_t)blk * a.K;
+        } else if (seq != nullptr && lane == 0) {
             for (int nu = 0; nu < a.K; ++nu) seq[nu] = -1;
         }
 
@@ -384,12 +647,5 @@ fsr_blocks_kernel(const KernelArgs a) {
         }
     }
 }
-
-// Host-side launch helpers (one translation unit per arithmetic type).
-struct LaunchInfo {
-    int grid;
-    int block_threads;
-    size_t smem;
-};
 
 }  // namespace fsrk

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/fsr.h"
+#include "fsr.h"
 #include "fsr_launch.h"
 
 struct fsr_handle {
