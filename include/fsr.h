@@ -54,8 +54,10 @@ extern "C" {
 
 /* Library configuration (fsr_create). */
 typedef struct fsr_config {
-    int device;              /* CUDA device ordinal the handle is bound to */
-    size_t workspace_bytes;  /* cap on device memory the handle may allocate; 0 = no cap */
+    int device;                  /* CUDA device ordinal the handle is bound to */
+    size_t workspace_bytes;      /* cap on device memory the handle may allocate; 0 = no cap */
+    const char *schedule_cache;  /* optional path of the batch-schedule cache written by
+                                    fsr_autotune_batch; read at creation; NULL = none */
 } fsr_config;
 
 /* Method parameters (Sec. II; defaults of Sec. IV: B=4, rho=0.7, gamma=0.5). */
@@ -119,6 +121,66 @@ int fsr_reconstruct_host(fsr_handle *h, const float *img, const uint8_t *mask,
 /* Number of target blocks N = ceil(height/B) * ceil(width/B) (Eq. 13);
  * 0 for invalid sizes. */
 long long fsr_num_blocks(int height, int width, int block);
+
+/* ---- Batch form: many images in one persistent launch ------------------
+ * The blocks of all images form one work list, images ordered by decreasing
+ * K (the long blocks start first); every warp of a persistent grid takes
+ * `chunk` entries at a time from a device counter.  Each block is computed by
+ * one warp with the same arithmetic as fsr_reconstruct, so results do not
+ * depend on the schedule and equal the single-image results bit for bit. */
+
+/* One image of a batch.  Pointer and geometry rules as in fsr_reconstruct. */
+typedef struct fsr_image_desc {
+    const float *img;    /* DEVICE float32, height x width, row pitch `pitch` elements */
+    const uint8_t *mask; /* DEVICE uint8, same geometry; nonzero = known */
+    float *out;          /* DEVICE float32, same geometry; may not overlap img or mask */
+    int height, width, pitch;
+    int iters;           /* K of this image, 0 <= K <= 65535 */
+    int16_t *seq_out;    /* optional DEVICE buffer of N_i*K_i selected indices, or NULL */
+} fsr_image_desc;
+
+/* Schedule of the persistent batch launch. */
+typedef struct fsr_schedule {
+    int warps;   /* warps per CTA = support blocks in flight per CTA (FP32: 12, or 4/6 for B = 4; FP64: 4) */
+    int chunk;   /* blocks a warp takes per counter increment, 1..64 */
+} fsr_schedule;
+
+typedef struct fsr_batch fsr_batch;
+
+/* Reconstruct n >= 1 images in one launch, asynchronously on `stream`.
+ * p supplies B, L, rho, gamma, freq_weight and precision; p->iters and
+ * p->seq_out are ignored (per image in d).  The work table lives in
+ * handle-owned device memory: a call waits on the host until the previous
+ * fsr_reconstruct_batch of this handle has finished before reusing it.
+ * Errors: as fsr_reconstruct, for every image; OOM for the table. */
+int fsr_reconstruct_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p, void *stream);
+
+/* Prepare a reusable batch: validates the images, uploads the work table to
+ * device memory owned by the batch and captures the launch (counter reset +
+ * kernel) in a CUDA graph, with the handle's current schedule.  The image
+ * buffers must stay valid while the batch is used.  Synchronous. */
+int fsr_batch_create(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p, fsr_batch **out);
+
+/* Replay the captured launch on `stream` (asynchronous).  Launches of one
+ * batch share its work counter: do not let two of them overlap on the device
+ * (launch them on one stream, or wait in between). */
+int fsr_batch_launch(fsr_batch *b, void *stream);
+
+/* Release a batch (waits for nothing; no launch of it may be in flight). */
+int fsr_batch_destroy(fsr_batch *b);
+
+/* Time every instantiated schedule (warps x chunk in {1, 2, 4, 8}) on this
+ * batch (its outputs are written), keep the fastest for (p->block,
+ * p->precision) in the handle and, if the handle has a schedule cache path,
+ * store it there.  best / best_ms may be NULL.  Synchronous.  The outputs of
+ * every schedule are identical, so the choice only affects time. */
+int fsr_autotune_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p,
+                       fsr_schedule *best, float *best_ms);
+
+/* Read or set the batch schedule used for (block, precision).
+ * Errors: INVALID_ARG, UNSUPPORTED (schedule not instantiated). */
+int fsr_get_schedule(const fsr_handle *h, int block, int precision, fsr_schedule *out);
+int fsr_set_schedule(fsr_handle *h, int block, int precision, const fsr_schedule *s);
 
 #ifdef __cplusplus
 }

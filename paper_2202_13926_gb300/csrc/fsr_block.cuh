@@ -37,18 +37,41 @@ constexpr int S = 32;                 // support size of this kernel family
 constexpr int TSTRIDE = S + 1;        // transpose buffer row stride
 constexpr unsigned FULL = 0xffffffffu;
 
-struct KernelArgs {
+// One image of a launch: device pointers (caller-owned) and geometry.
+struct ImageArgs {
     const float* img;
     const uint8_t* mask;
     float* out;
-    int16_t* seq;        // optional: N*K selected indices
-    long long nblocks;   // N
-    int H, W, pitch;     // image geometry (pitch in elements, shared by all three)
-    int nbx;             // ceil(W / B)
+    int16_t* seq;        // optional: N*K selected indices of this image
+    int H, W, pitch;     // geometry (pitch in elements, shared by img, mask, out)
+    int nbx;             // ceil(W / B): blocks per block row
+    int K;               // iterations of this image
+};
+
+// Parameters shared by every image of a launch.
+struct MethodArgs {
     int L;               // border
-    int K;               // iterations
     float rho, gamma;
     int freq_weight;
+};
+
+// Single image, static schedule.
+struct KernelArgs {
+    ImageArgs im;
+    long long nblocks;   // N
+    MethodArgs mth;
+};
+
+// Many images, dynamic schedule: warps take chunks of the concatenated block
+// list (images ordered by decreasing K) from a device counter.
+struct BatchArgs {
+    const ImageArgs* images;     // n images, device memory
+    const long long* first;      // n + 1 prefix sums of the block counts
+    int n;
+    long long total;             // first[n]
+    unsigned long long* counter; // zero at launch
+    int chunk;                   // blocks taken per counter increment
+    MethodArgs mth;
 };
 
 // cos(pi t / 16) for t = 0..8 (mathematical constants).
@@ -188,7 +211,7 @@ struct BlockState {
 // On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
 // row k in zr/zi and every row of W is in Wd twice in a row.
 template <typename T, int WS>
-__device__ __forceinline__ bool prepare_block(const KernelArgs& a, int y0, int x0, int lane,
+__device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
                                               const T* __restrict__ sw0,
                                               typename Vec2<T>::type* Wd,
                                               T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
@@ -570,30 +593,18 @@ __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double
     }
 }
 
-template <typename T, int B, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1)
-fsr_blocks_kernel(const KernelArgs a) {
+// Shared-memory tables of one CTA: Eqs. (5) and (9) and cos/sin(2 pi t / S).
+template <typename T>
+__device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf,
+                                           typename Vec2<T>::type* scs) {
     using T2 = typename Vec2<T>::type;
-    using Lay = SmemLayout<T>;
-    constexpr int P = TargetPix<B>::P;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
-    T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
-    T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
-    T2* rowbuf = Wd + Lay::w_elems;
-
-    // Tables of Eqs. (5) and (9) and cos/sin(2 pi t / S), per CTA.
     const T half = T(S) / T(2);
     for (int i = threadIdx.x; i < S * S; i += blockDim.x) {
         const int m = i / S, n = i % S;
         const T dm = T(m) - T(S - 1) / T(2), dn = T(n) - T(S - 1) / T(2);
-        sw0[i] = pow(T(a.rho), sqrt(dm * dm + dn * dn));
+        sw0[i] = pow(T(mth.rho), sqrt(dm * dm + dn * dn));
         T wfv = T(1);
-        if (a.freq_weight) {
+        if (mth.freq_weight) {
             const T kt = half - fabs(T(m) - half), lt = half - fabs(T(n) - half);
             const T r = sqrt(kt * kt / T(S * S) + lt * lt / T(S * S));
             const T b = T(1) - sqrt(T(2)) * r;
@@ -607,43 +618,113 @@ fsr_blocks_kernel(const KernelArgs a) {
         v.y = T(sin_2pi32(t));
         scs[t] = v;
     }
+}
+
+// Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
+template <typename T, int B>
+__device__ __forceinline__ void process_block(const ImageArgs& im, long long blk, int L, T gamma,
+                                              const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
+                                              typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
+                                              int lane) {
+    constexpr int P = TargetPix<B>::P;
+    const int by = (int)(blk / im.nbx);
+    const int bx = (int)(blk - (long long)by * im.nbx);
+    const int y0 = by * B - L, x0 = bx * B - L;
+
+    T zr[S], zi[S];
+    BlockState<T> st;
+    T gacc[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) gacc[q] = T(0);
+
+    int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
+    if (prepare_block<T, SmemLayout<T>::WS>(im, y0, x0, lane, sw0, Wd, zr, zi, st)) {
+        iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
+        __syncwarp();   // W area free for the next block
+    } else if (seq != nullptr && lane == 0) {
+        for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+    }
+
+    // ---- a9: write-back of the B x B target ----
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int pidx = lane + 32 * q;
+        if (pidx < B * B) {
+            const int ty = by * B + pidx / B, tx = bx * B + pidx % B;
+            if (ty < im.H && tx < im.W) {
+                const size_t off = (size_t)ty * im.pitch + tx;
+                const bool kn = __ldg(im.mask + off) != 0;
+                im.out[off] = kn ? __ldg(im.img + off) : (float)gacc[q];
+            }
+        }
+    }
+}
+
+// Register budget: FP32 CTAs are sized so that 12 warps share an SM, FP64
+// runs one CTA per SM.
+template <typename T, int WARPS> struct MinBlocks { static constexpr int value = 1; };
+template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value = 12 / WARPS; };
+
+template <typename T, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
+fsr_blocks_kernel(const KernelArgs a) {
+    using T2 = typename Vec2<T>::type;
+    using Lay = SmemLayout<T>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
+    T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
+    T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
+    T2* rowbuf = Wd + Lay::w_elems;
+
+    cta_tables<T>(a.mth, sw0, swf, scs);
     __syncthreads();
 
-    const T gamma = T(a.gamma);
-    const int L = a.L;
-
+    const T gamma = T(a.mth.gamma);
     for (long long blk = (long long)blockIdx.x * WARPS + warp; blk < a.nblocks;
-         blk += (long long)gridDim.x * WARPS) {
-        const int by = (int)(blk / a.nbx);
-        const int bx = (int)(blk - (long long)by * a.nbx);
-        const int y0 = by * B - L, x0 = bx * B - L;
+         blk += (long long)gridDim.x * WARPS)
+        process_block<T, B>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, lane);
+}
 
-        T zr[S], zi[S];
-        BlockState<T> st;
-        T gacc[P];
-#pragma unroll
-        for (int q = 0; q < P; ++q) gacc[q] = T(0);
+// Batch form: every warp takes `chunk` consecutive entries of the block list
+// at a time; images are ordered by decreasing K so the long blocks start first.
+template <typename T, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
+fsr_batch_kernel(const BatchArgs a) {
+    using T2 = typename Vec2<T>::type;
+    using Lay = SmemLayout<T>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
+    T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
+    T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
+    T2* rowbuf = Wd + Lay::w_elems;
 
-        int16_t* seq = a.seq ? a.seq + (size_t)blk * a.K : nullptr;
-        if (prepare_block<T, Lay::WS>(a, y0, x0, lane, sw0, Wd, zr, zi, st)) {
-            iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, a.K, L, lane, seq, gacc);
-            __syncwarp();   // W area free for the next block
-        } else if (seq != nullptr && lane == 0) {
-            for (int nu = 0; nu < a.K; ++nu) seq[nu] = -1;
-        }
+    cta_tables<T>(a.mth, sw0, swf, scs);
+    __syncthreads();
 
-        // ---- a9: write-back of the B x B target ----
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const int pidx = lane + 32 * q;
-            if (pidx < B * B) {
-                const int ty = by * B + pidx / B, tx = bx * B + pidx % B;
-                if (ty < a.H && tx < a.W) {
-                    const size_t off = (size_t)ty * a.pitch + tx;
-                    const bool kn = __ldg(a.mask + off) != 0;
-                    a.out[off] = kn ? __ldg(a.img + off) : (float)gacc[q];
-                }
+    const T gamma = T(a.mth.gamma);
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= (unsigned long long)a.total) break;
+        const long long end = min((long long)base + a.chunk, a.total);
+        for (long long item = (long long)base; item < end; ++item) {
+            // image of this entry: last i with first[i] <= item
+            int lo = 0, hi = a.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.first + mid) <= item) lo = mid;
+                else hi = mid - 1;
             }
+            const ImageArgs im = a.images[lo];
+            process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
+                                rowbuf, lane);
         }
     }
 }

@@ -1,27 +1,55 @@
-// C-ABI of the GB300 FSR library: handle management, argument checks and
-// dispatch to the per-block kernels.  Declarations and contracts: include/fsr.h.
+// C-ABI of the GB300 FSR library: handles, argument checks, the batch form
+// (work tables, CUDA-graph plans, schedule autotuner) and dispatch to the
+// kernels.  Declarations and contracts: include/fsr.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
+#include <string>
+#include <vector>
 
 #include "fsr.h"
 #include "fsr_launch.h"
 
+namespace {
+
+constexpr int kNumB = 4;   // B in {2, 4, 8, 16}
+int b_index(int B) { return B == 2 ? 0 : B == 4 ? 1 : B == 8 ? 2 : B == 16 ? 3 : -1; }
+
+}  // namespace
+
 struct fsr_handle {
     int device = 0;
     int sm_count = 0;
-    int cc_major = 0, cc_minor = 0;
+    char device_name[256] = {0};
     size_t ws_cap = 0;       // 0 = no cap
     size_t ws_used = 0;
     char err[512] = {0};
+    std::string cache_path;
+    // batch schedules per [precision][B]
+    fsrk::Schedule sched[2][kNumB] = {{{12, 1}, {12, 1}, {12, 1}, {12, 1}}, {{4, 1}, {4, 1}, {4, 1}, {4, 1}}};
     // device staging buffers of fsr_reconstruct_host
     float* d_img = nullptr;
     uint8_t* d_mask = nullptr;
     float* d_out = nullptr;
     size_t stage_pixels = 0;
+    // work table of the one-shot batch entry point
+    void* d_table = nullptr;
+    void* h_table = nullptr;       // pinned host staging of the table
+    size_t table_bytes = 0;
+    cudaEvent_t table_free = nullptr;
+};
+
+struct fsr_batch {
+    fsr_handle* h = nullptr;
+    void* d_table = nullptr;
+    size_t bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -67,16 +95,12 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
     return pa < pb + nb && pb < pa + na;
 }
 
-int check_params(fsr_handle* h, int height, int width, int pitch, const fsr_params* p) {
+int check_method(fsr_handle* h, const fsr_params* p) {
     if (!p) return fail(h, FSR_ERR_INVALID_ARG, "params is NULL");
-    if (height <= 0 || width <= 0) return fail(h, FSR_ERR_INVALID_ARG, "height/width must be > 0 (got %d x %d)", height, width);
-    if (pitch < width) return fail(h, FSR_ERR_INVALID_ARG, "pitch (%d) < width (%d)", pitch, width);
     if (p->block <= 0 || p->border < 0) return fail(h, FSR_ERR_INVALID_ARG, "block must be > 0 and border >= 0");
     if (p->block + 2 * p->border != fsrk::S)
         return fail(h, FSR_ERR_UNSUPPORTED, "support B + 2L = %d; this build implements S = 32", p->block + 2 * p->border);
-    if (p->block != 2 && p->block != 4 && p->block != 8 && p->block != 16)
-        return fail(h, FSR_ERR_UNSUPPORTED, "block %d not in {2, 4, 8, 16}", p->block);
-    if (p->iters < 0 || p->iters > 65535) return fail(h, FSR_ERR_INVALID_ARG, "iters %d out of [0, 65535]", p->iters);
+    if (b_index(p->block) < 0) return fail(h, FSR_ERR_UNSUPPORTED, "block %d not in {2, 4, 8, 16}", p->block);
     if (!(p->rho > 0.f && p->rho <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "rho must be in (0, 1]");
     if (!(p->gamma > 0.f && p->gamma <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "gamma must be in (0, 1]");
     if (p->freq_weight != 0 && p->freq_weight != 1) return fail(h, FSR_ERR_INVALID_ARG, "freq_weight must be 0 or 1");
@@ -85,28 +109,206 @@ int check_params(fsr_handle* h, int height, int width, int pitch, const fsr_para
     return FSR_OK;
 }
 
-int enqueue(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width,
-            int pitch, const fsr_params* p, float* out, cudaStream_t stream) {
+int check_image(fsr_handle* h, const float* img, const uint8_t* mask, const float* out, int height, int width,
+                int pitch, int iters, bool device_ptrs, int index) {
+    if (!img || !mask || !out) return fail(h, FSR_ERR_INVALID_ARG, "image %d: img, mask and out must be non-NULL", index);
+    if (height <= 0 || width <= 0)
+        return fail(h, FSR_ERR_INVALID_ARG, "image %d: height/width must be > 0 (got %d x %d)", index, height, width);
+    if (pitch < width) return fail(h, FSR_ERR_INVALID_ARG, "image %d: pitch (%d) < width (%d)", index, pitch, width);
+    if (iters < 0 || iters > 65535) return fail(h, FSR_ERR_INVALID_ARG, "image %d: iters %d out of [0, 65535]", index, iters);
+    if (device_ptrs) {
+        const size_t n = (size_t)(height - 1) * pitch + width;
+        if (ranges_overlap(out, n * sizeof(float), img, n * sizeof(float)) ||
+            ranges_overlap(out, n * sizeof(float), mask, n))
+            return fail(h, FSR_ERR_INVALID_ARG, "image %d: out overlaps img or mask", index);
+    }
+    return FSR_OK;
+}
+
+fsrk::MethodArgs method_args(const fsr_params* p) {
+    fsrk::MethodArgs m;
+    m.L = p->border;
+    m.rho = p->rho;
+    m.gamma = p->gamma;
+    m.freq_weight = p->freq_weight;
+    return m;
+}
+
+fsrk::ImageArgs image_args(const float* img, const uint8_t* mask, float* out, int16_t* seq, int height, int width,
+                           int pitch, int iters, int B) {
+    fsrk::ImageArgs im;
+    im.img = img;
+    im.mask = mask;
+    im.out = out;
+    im.seq = seq;
+    im.H = height;
+    im.W = width;
+    im.pitch = pitch;
+    im.nbx = (width + B - 1) / B;
+    im.K = iters;
+    return im;
+}
+
+int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                   const fsr_params* p, float* out, cudaStream_t stream) {
     fsrk::KernelArgs a;
-    a.img = img;
-    a.mask = mask;
-    a.out = out;
-    a.seq = p->seq_out;
-    a.H = height;
-    a.W = width;
-    a.pitch = pitch;
-    a.nbx = (width + p->block - 1) / p->block;
-    a.nblocks = (long long)a.nbx * ((height + p->block - 1) / p->block);
-    a.L = p->border;
-    a.K = p->iters;
-    a.rho = p->rho;
-    a.gamma = p->gamma;
-    a.freq_weight = p->freq_weight;
-    cudaError_t e = (p->precision == FSR_FP64_DEBUG)
-                        ? fsrk::launch_fp64(a, p->block, h->sm_count, stream)
-                        : fsrk::launch_fp32(a, p->block, h->sm_count, stream);
+    a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
+    a.nblocks = (long long)a.im.nbx * ((height + p->block - 1) / p->block);
+    a.mth = method_args(p);
+    cudaError_t e = (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_single_fp64(a, p->block, h->sm_count, stream)
+                                                      : fsrk::launch_single_fp32(a, p->block, h->sm_count, stream);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return ok(h);
+}
+
+// ---- batch work tables -----------------------------------------------------
+// Layout in one device allocation: [counter u64][first: (n+1) x i64][images: n x ImageArgs]
+
+size_t table_bytes(int n) {
+    size_t b = sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1);
+    b = (b + 15) & ~(size_t)15;
+    return b + sizeof(fsrk::ImageArgs) * (size_t)n;
+}
+
+int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p) {
+    if (n < 1) return fail(h, FSR_ERR_INVALID_ARG, "batch needs n >= 1 images (got %d)", n);
+    if (!d) return fail(h, FSR_ERR_INVALID_ARG, "descs is NULL");
+    int r = check_method(h, p);
+    if (r != FSR_OK) return r;
+    for (int i = 0; i < n; ++i) {
+        r = check_image(h, d[i].img, d[i].mask, d[i].out, d[i].height, d[i].width, d[i].pitch, d[i].iters, true, i);
+        if (r != FSR_OK) return r;
+    }
+    return FSR_OK;
+}
+
+// Fill the host image of the table; returns the total number of blocks.
+long long build_table(int n, const fsr_image_desc* d, const fsr_params* p, void* host) {
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a].iters > d[b].iters; });
+    char* base = static_cast<char*>(host);
+    auto* counter = reinterpret_cast<unsigned long long*>(base);
+    auto* first = reinterpret_cast<long long*>(base + sizeof(unsigned long long));
+    size_t off = (sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1) + 15) & ~(size_t)15;
+    auto* imgs = reinterpret_cast<fsrk::ImageArgs*>(base + off);
+    *counter = 0;
+    long long total = 0;
+    for (int j = 0; j < n; ++j) {
+        const fsr_image_desc& x = d[order[j]];
+        imgs[j] = image_args(x.img, x.mask, x.out, x.seq_out, x.height, x.width, x.pitch, x.iters, p->block);
+        first[j] = total;
+        total += fsr_num_blocks(x.height, x.width, p->block);
+    }
+    first[n] = total;
+    return total;
+}
+
+fsrk::BatchArgs batch_args(void* d_table, int n, long long total, const fsr_params* p, int chunk) {
+    char* base = static_cast<char*>(d_table);
+    size_t off = (sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1) + 15) & ~(size_t)15;
+    fsrk::BatchArgs a;
+    a.counter = reinterpret_cast<unsigned long long*>(base);
+    a.first = reinterpret_cast<const long long*>(base + sizeof(unsigned long long));
+    a.images = reinterpret_cast<const fsrk::ImageArgs*>(base + off);
+    a.n = n;
+    a.total = total;
+    a.chunk = chunk;
+    a.mth = method_args(p);
+    return a;
+}
+
+cudaError_t launch_batch(const fsrk::BatchArgs& a, const fsr_params* p, fsrk::Schedule sc, int sm_count,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    return (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(a, p->block, sc, sm_count, s)
+                                             : fsrk::launch_batch_fp32(a, p->block, sc, sm_count, s);
+}
+
+bool schedule_ok(int precision, int B, const fsrk::Schedule& s) {
+    return s.chunk >= 1 && s.chunk <= 64 && fsrk::batch_schedule_supported(precision == FSR_FP64_DEBUG, B, s.warps);
+}
+
+void read_schedule_cache(fsr_handle* h) {
+    if (h->cache_path.empty()) return;
+    FILE* f = fopen(h->cache_path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char name[256];
+        int prec, B, warps, chunk;
+        if (sscanf(line, "%255[^|]|%d|%d|%d|%d", name, &prec, &B, &warps, &chunk) == 5 &&
+            strcmp(name, h->device_name) == 0 && (prec == 0 || prec == 1) && b_index(B) >= 0) {
+            fsrk::Schedule s{warps, chunk};
+            if (schedule_ok(prec, B, s)) h->sched[prec][b_index(B)] = s;
+        }
+    }
+    fclose(f);
+}
+
+void write_schedule_cache(const fsr_handle* h) {
+    if (h->cache_path.empty()) return;
+    FILE* f = fopen(h->cache_path.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "# device|precision|B|warps|chunk  (fsr batch schedules)\n");
+    const int Bs[kNumB] = {2, 4, 8, 16};
+    for (int prec = 0; prec < 2; ++prec)
+        for (int i = 0; i < kNumB; ++i)
+            fprintf(f, "%s|%d|%d|%d|%d\n", h->device_name, prec, Bs[i], h->sched[prec][i].warps, h->sched[prec][i].chunk);
+    fclose(f);
+}
+
+int make_plan(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p, fsrk::Schedule sc,
+              fsr_batch** out) {
+    const size_t bytes = table_bytes(n);
+    if (h->ws_cap && h->ws_used + bytes > h->ws_cap)
+        return fail(h, FSR_ERR_OOM, "batch table of %zu bytes exceeds the workspace cap of %zu", bytes, h->ws_cap);
+    std::vector<char> host(bytes);
+    const long long total = build_table(n, d, p, host.data());
+    fsr_batch* b = new (std::nothrow) fsr_batch();
+    if (!b) return fail(h, FSR_ERR_OOM, "host allocation of the batch failed");
+    b->h = h;
+    b->bytes = bytes;
+    cudaError_t e = cudaMalloc(&b->d_table, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(h, FSR_ERR_OOM, "cudaMalloc of the batch table (%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    cudaStream_t cs = nullptr;
+    if ((e = cudaMemcpy(b->d_table, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaFree(b->d_table);
+        delete b;
+        return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
+    }
+    const fsrk::BatchArgs a = batch_args(b->d_table, n, total, p, sc.chunk);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t el = launch_batch(a, p, sc, h->sm_count, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (b->graph) cudaGraphDestroy(b->graph);
+        cudaFree(b->d_table);
+        delete b;
+        return fail(h, FSR_ERR_CUDA, "capturing the batch launch: %s", cudaGetErrorString(e));
+    }
+    h->ws_used += bytes;
+    *out = b;
+    return ok(h);
+}
+
+void free_plan(fsr_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_table);
+    if (b->h) b->h->ws_used -= b->bytes;
+    delete b;
 }
 
 }  // namespace
@@ -131,15 +333,22 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
     if (!(prop.major == 10 && prop.minor == 3))
         return fail(nullptr, FSR_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only",
                     cfg->device, prop.major, prop.minor);
-    if ((e = fsrk::configure_fp32()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess)
+    if ((e = fsrk::configure_fp32()) != cudaSuccess || (e = fsrk::configure_fp32_batch()) != cudaSuccess ||
+        (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
+        (e = fsrk::configure_fp64_batch()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));
     fsr_handle* h = new (std::nothrow) fsr_handle();
     if (!h) return fail(nullptr, FSR_ERR_OOM, "host allocation of the handle failed");
+    if ((e = cudaEventCreateWithFlags(&h->table_free, cudaEventDisableTiming)) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, FSR_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
     h->device = cfg->device;
     h->sm_count = prop.multiProcessorCount;
-    h->cc_major = prop.major;
-    h->cc_minor = prop.minor;
+    snprintf(h->device_name, sizeof h->device_name, "%s", prop.name);
     h->ws_cap = cfg->workspace_bytes;
+    if (cfg->schedule_cache) h->cache_path = cfg->schedule_cache;
+    read_schedule_cache(h);
     *out = h;
     g_create_err[0] = 0;
     return FSR_OK;
@@ -153,6 +362,9 @@ int fsr_destroy(fsr_handle* h) {
             cudaFree(h->d_img);
             cudaFree(h->d_mask);
             cudaFree(h->d_out);
+            cudaFree(h->d_table);
+            if (h->h_table) cudaFreeHost(h->h_table);
+            if (h->table_free) cudaEventDestroy(h->table_free);
         }
     }
     delete h;
@@ -166,27 +378,25 @@ long long fsr_num_blocks(int height, int width, int block) {
     return (long long)((height + block - 1) / block) * ((width + block - 1) / block);
 }
 
-int fsr_reconstruct(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width,
-                    int pitch, const fsr_params* p, float* out, void* stream) {
+int fsr_reconstruct(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                    const fsr_params* p, float* out, void* stream) {
     if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
-    if (!img || !mask || !out) return fail(h, FSR_ERR_INVALID_ARG, "img, mask and out must be non-NULL");
-    int r = check_params(h, height, width, pitch, p);
+    int r = check_method(h, p);
     if (r != FSR_OK) return r;
-    const size_t n = (size_t)(height - 1) * pitch + width;
-    if (ranges_overlap(out, n * sizeof(float), img, n * sizeof(float)) ||
-        ranges_overlap(out, n * sizeof(float), mask, n))
-        return fail(h, FSR_ERR_INVALID_ARG, "out overlaps img or mask");
+    r = check_image(h, img, mask, out, height, width, pitch, p->iters, true, 0);
+    if (r != FSR_OK) return r;
     DeviceGuard g;
     cudaError_t e = g.set(h->device);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-    return enqueue(h, img, mask, height, width, pitch, p, out, static_cast<cudaStream_t>(stream));
+    return enqueue_single(h, img, mask, height, width, pitch, p, out, static_cast<cudaStream_t>(stream));
 }
 
-int fsr_reconstruct_host(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width,
-                         int pitch, const fsr_params* p, float* out, void* stream) {
+int fsr_reconstruct_host(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                         const fsr_params* p, float* out, void* stream) {
     if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
-    if (!img || !mask || !out) return fail(h, FSR_ERR_INVALID_ARG, "img, mask and out must be non-NULL");
-    int r = check_params(h, height, width, pitch, p);
+    int r = check_method(h, p);
+    if (r != FSR_OK) return r;
+    r = check_image(h, img, mask, out, height, width, pitch, p->iters, false, 0);
     if (r != FSR_OK) return r;
     DeviceGuard g;
     cudaError_t e = g.set(h->device);
@@ -197,16 +407,23 @@ int fsr_reconstruct_host(fsr_handle* h, const float* img, const uint8_t* mask, i
         const size_t have = h->stage_pixels * (2 * sizeof(float) + 1);
         if (h->ws_cap && h->ws_used - have + need > h->ws_cap)
             return fail(h, FSR_ERR_OOM, "staging %zu bytes exceeds the workspace cap of %zu", need, h->ws_cap);
-        cudaFree(h->d_img); cudaFree(h->d_mask); cudaFree(h->d_out);
-        h->d_img = nullptr; h->d_mask = nullptr; h->d_out = nullptr;
+        cudaFree(h->d_img);
+        cudaFree(h->d_mask);
+        cudaFree(h->d_out);
+        h->d_img = nullptr;
+        h->d_mask = nullptr;
+        h->d_out = nullptr;
         h->ws_used -= have;
         h->stage_pixels = 0;
-        if (cudaMalloc(&h->d_img, npix * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&h->d_mask, npix) != cudaSuccess ||
+        if (cudaMalloc(&h->d_img, npix * sizeof(float)) != cudaSuccess || cudaMalloc(&h->d_mask, npix) != cudaSuccess ||
             cudaMalloc(&h->d_out, npix * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(h->d_img); cudaFree(h->d_mask); cudaFree(h->d_out);
-            h->d_img = nullptr; h->d_mask = nullptr; h->d_out = nullptr;
+            cudaFree(h->d_img);
+            cudaFree(h->d_mask);
+            cudaFree(h->d_out);
+            h->d_img = nullptr;
+            h->d_mask = nullptr;
+            h->d_out = nullptr;
             return fail(h, FSR_ERR_OOM, "cudaMalloc of %zu staging bytes failed", need);
         }
         h->stage_pixels = npix;
@@ -215,16 +432,168 @@ int fsr_reconstruct_host(fsr_handle* h, const float* img, const uint8_t* mask, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((e = cudaMemcpy2DAsync(h->d_img, width * sizeof(float), img, (size_t)pitch * sizeof(float),
                                width * sizeof(float), height, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpy2DAsync(h->d_mask, width, mask, (size_t)pitch, width, height,
-                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        (e = cudaMemcpy2DAsync(h->d_mask, width, mask, (size_t)pitch, width, height, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "host-to-device copy: %s", cudaGetErrorString(e));
-    r = enqueue(h, h->d_img, h->d_mask, height, width, width, p, h->d_out, s);
+    r = enqueue_single(h, h->d_img, h->d_mask, height, width, width, p, h->d_out, s);
     if (r != FSR_OK) return r;
     if ((e = cudaMemcpy2DAsync(out, (size_t)pitch * sizeof(float), h->d_out, width * sizeof(float),
                                width * sizeof(float), height, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "device-to-host copy: %s", cudaGetErrorString(e));
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return ok(h);
+}
+
+int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p, void* stream) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    int r = check_batch(h, n, d, p);
+    if (r != FSR_OK) return r;
+    DeviceGuard g;
+    cudaError_t e = g.set(h->device);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    // the previous batch of this handle must be done with the table
+    if ((e = cudaEventSynchronize(h->table_free)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "waiting for the previous batch: %s", cudaGetErrorString(e));
+    const size_t bytes = table_bytes(n);
+    if (bytes > h->table_bytes) {
+        if (h->ws_cap && h->ws_used - h->table_bytes + bytes > h->ws_cap)
+            return fail(h, FSR_ERR_OOM, "batch table of %zu bytes exceeds the workspace cap of %zu", bytes, h->ws_cap);
+        cudaFree(h->d_table);
+        if (h->h_table) cudaFreeHost(h->h_table);
+        h->d_table = nullptr;
+        h->h_table = nullptr;
+        h->ws_used -= h->table_bytes;
+        h->table_bytes = 0;
+        if (cudaMalloc(&h->d_table, bytes) != cudaSuccess || cudaMallocHost(&h->h_table, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->d_table);
+            if (h->h_table) cudaFreeHost(h->h_table);
+            h->d_table = nullptr;
+            h->h_table = nullptr;
+            return fail(h, FSR_ERR_OOM, "allocating the batch table (%zu bytes) failed", bytes);
+        }
+        h->table_bytes = bytes;
+        h->ws_used += bytes;
+    }
+    const long long total = build_table(n, d, p, h->h_table);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const fsrk::Schedule sc = h->sched[p->precision][b_index(p->block)];
+    if ((e = cudaMemcpyAsync(h->d_table, h->h_table, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
+    if ((e = launch_batch(batch_args(h->d_table, n, total, p, sc.chunk), p, sc, h->sm_count, s)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+    if ((e = cudaEventRecord(h->table_free, s)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    return ok(h);
+}
+
+int fsr_batch_create(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p, fsr_batch** out) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    if (!out) return fail(h, FSR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int r = check_batch(h, n, d, p);
+    if (r != FSR_OK) return r;
+    DeviceGuard g;
+    cudaError_t e = g.set(h->device);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return make_plan(h, n, d, p, h->sched[p->precision][b_index(p->block)], out);
+}
+
+int fsr_batch_launch(fsr_batch* b, void* stream) {
+    if (!b) return fail(nullptr, FSR_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard g;
+    cudaError_t e = g.set(b->h->device);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(b->h, FSR_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return ok(b->h);
+}
+
+int fsr_batch_destroy(fsr_batch* b) {
+    if (!b) return FSR_OK;
+    DeviceGuard g;
+    g.set(b->h->device);
+    free_plan(b);
+    return FSR_OK;
+}
+
+int fsr_get_schedule(const fsr_handle* h, int block, int precision, fsr_schedule* out) {
+    if (!h || !out || b_index(block) < 0 || (precision != FSR_FP32 && precision != FSR_FP64_DEBUG))
+        return FSR_ERR_INVALID_ARG;
+    const fsrk::Schedule& s = h->sched[precision][b_index(block)];
+    out->warps = s.warps;
+    out->chunk = s.chunk;
+    return FSR_OK;
+}
+
+int fsr_set_schedule(fsr_handle* h, int block, int precision, const fsr_schedule* s) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    if (!s || b_index(block) < 0 || (precision != FSR_FP32 && precision != FSR_FP64_DEBUG))
+        return fail(h, FSR_ERR_INVALID_ARG, "bad block, precision or schedule pointer");
+    const fsrk::Schedule sc{s->warps, s->chunk};
+    if (!schedule_ok(precision, block, sc))
+        return fail(h, FSR_ERR_UNSUPPORTED, "schedule warps=%d chunk=%d is not instantiated for B=%d", s->warps,
+                    s->chunk, block);
+    h->sched[precision][b_index(block)] = sc;
+    return ok(h);
+}
+
+int fsr_autotune_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p, fsr_schedule* best,
+                       float* best_ms) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    int r = check_batch(h, n, d, p);
+    if (r != FSR_OK) return r;
+    DeviceGuard g;
+    cudaError_t e = g.set(h->device);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    cudaStream_t s = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "autotune setup: %s", cudaGetErrorString(e));
+    const int warps_c[3] = {12, 6, 4};
+    const int chunk_c[4] = {1, 2, 4, 8};
+    fsrk::Schedule win = h->sched[p->precision][b_index(p->block)];
+    float win_ms = -1.f;
+    int rc = FSR_OK;
+    for (int wi = 0; wi < 3 && rc == FSR_OK; ++wi) {
+        for (int ci = 0; ci < 4 && rc == FSR_OK; ++ci) {
+            const fsrk::Schedule sc{warps_c[wi], chunk_c[ci]};
+            if (!schedule_ok(p->precision, p->block, sc)) continue;
+            fsr_batch* plan = nullptr;
+            rc = make_plan(h, n, d, p, sc, &plan);
+            if (rc != FSR_OK) break;
+            float ms = 0.f;
+            // one warm-up launch, then the mean of two timed launches
+            e = cudaGraphLaunch(plan->exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = cudaGraphLaunch(plan->exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            free_plan(plan);
+            if (e != cudaSuccess) {
+                rc = fail(h, FSR_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+                break;
+            }
+            ms *= 0.5f;
+            if (win_ms < 0.f || ms < win_ms) {
+                win_ms = ms;
+                win = sc;
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaStreamDestroy(s);
+    if (rc != FSR_OK) return rc;
+    h->sched[p->precision][b_index(p->block)] = win;
+    write_schedule_cache(h);
+    if (best) {
+        best->warps = win.warps;
+        best->chunk = win.chunk;
+    }
+    if (best_ms) *best_ms = win_ms;
     return ok(h);
 }
 

@@ -1,52 +1,31 @@
-// FP32 instantiations of the per-block FSR kernel (the production path).
+// FP32 single-image instantiations (the production path): 12 warps per CTA,
+// one CTA per SM (12 x 17.2 KB of W rows + 8.4 KB of tables).
 #include "fsr_launch.h"
 
 namespace fsrk {
-namespace {
-
-constexpr int kWarps32 = 12;   // 12 x 16.9 KB of W rows + 8.4 KB tables per CTA
-
-template <int B>
-cudaError_t configure_one() {
-    return cudaFuncSetAttribute(fsr_blocks_kernel<float, B, kWarps32>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SmemLayout<float>::bytes(kWarps32));
-}
-
-template <int B>
-cudaError_t launch_one(const KernelArgs& a, int sm_count, cudaStream_t stream) {
-    const size_t smem = SmemLayout<float>::bytes(kWarps32);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, fsr_blocks_kernel<float, B, kWarps32>, kWarps32 * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long need = (a.nblocks + kWarps32 - 1) / kWarps32;
-    long long grid = (long long)sm_count * per_sm;
-    if (need < grid) grid = need;
-    if (grid < 1) grid = 1;
-    fsr_blocks_kernel<float, B, kWarps32><<<(unsigned)grid, kWarps32 * 32, smem, stream>>>(a);
-    return cudaGetLastError();
-}
-
-}  // namespace
 
 cudaError_t configure_fp32() {
     cudaError_t e;
-    if ((e = configure_one<2>()) != cudaSuccess) return e;
-    if ((e = configure_one<4>()) != cudaSuccess) return e;
-    if ((e = configure_one<8>()) != cudaSuccess) return e;
-    return configure_one<16>();
+    if ((e = configure_single<float, 2, 12>()) != cudaSuccess) return e;
+    if ((e = configure_single<float, 4, 12>()) != cudaSuccess) return e;
+    if ((e = configure_single<float, 8, 12>()) != cudaSuccess) return e;
+    return configure_single<float, 16, 12>();
 }
 
-cudaError_t launch_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream) {
+cudaError_t launch_single_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream) {
     switch (B) {
-        case 2: return launch_one<2>(a, sm_count, stream);
-        case 4: return launch_one<4>(a, sm_count, stream);
-        case 8: return launch_one<8>(a, sm_count, stream);
-        case 16: return launch_one<16>(a, sm_count, stream);
+        case 2: return launch_single_t<float, 2, 12>(a, sm_count, stream);
+        case 4: return launch_single_t<float, 4, 12>(a, sm_count, stream);
+        case 8: return launch_single_t<float, 8, 12>(a, sm_count, stream);
+        case 16: return launch_single_t<float, 16, 12>(a, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+bool batch_schedule_supported(int fp64, int B, int warps) {
+    if (B != 2 && B != 4 && B != 8 && B != 16) return false;
+    if (fp64) return warps == 4;
+    return warps == 12 || (B == 4 && (warps == 4 || warps == 6));
 }
 
 }  // namespace fsrk

@@ -1,4 +1,5 @@
-// Launchers of the per-block FSR kernels (one per arithmetic type).
+// Launchers of the FSR kernels.  Each translation unit instantiates one
+// arithmetic type / schedule family; fsr_capi.cu dispatches.
 #pragma once
 
 #include <cstddef>
@@ -8,14 +9,80 @@
 
 namespace fsrk {
 
-// Sets the dynamic shared-memory limit of every instantiation; call once per
-// device with that device current.  Returns cudaSuccess or the first error.
-cudaError_t configure_fp32();
-cudaError_t configure_fp64();
+// A persistent schedule: warps per CTA (one support block per warp) and the
+// number of blocks a warp takes per work-counter increment (batch form).
+struct Schedule {
+    int warps;
+    int chunk;
+};
 
-// Enqueue the reconstruction of a.nblocks blocks with target size B on
-// `stream`, on a persistent grid sized from the SM count.
-cudaError_t launch_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
-cudaError_t launch_fp64(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
+// Sets the dynamic shared-memory limit of every instantiation of the family;
+// call once per device with that device current.
+cudaError_t configure_fp32();
+cudaError_t configure_fp32_batch();
+cudaError_t configure_fp32_sched();
+cudaError_t configure_fp64();
+cudaError_t configure_fp64_batch();
+
+// Single image, static schedule, 12 (FP32) or 4 (FP64) warps per CTA.
+cudaError_t launch_single_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
+cudaError_t launch_single_fp64(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
+
+// Batch form.  Returns cudaErrorNotSupported for a schedule that is not
+// instantiated (see batch_schedule_supported).
+cudaError_t launch_batch_fp32(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
+cudaError_t launch_batch_fp32_sched(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
+cudaError_t launch_batch_fp64(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
+
+// Warps-per-CTA values instantiated for (precision, B): FP32 has 12 for every
+// B and also 4 and 6 for B = 4; FP64 has 4.
+bool batch_schedule_supported(int fp64, int B, int warps);
+
+// Persistent grid: resident CTAs per SM x SMs, capped by the work available.
+template <typename Kernel>
+cudaError_t persistent_grid(Kernel k, int warps, size_t smem, long long work_warps, int sm_count, int* grid) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long need = (work_warps + warps - 1) / warps;
+    long long g = (long long)sm_count * per_sm;
+    if (need < g) g = need;
+    if (g < 1) g = 1;
+    *grid = (int)g;
+    return cudaSuccess;
+}
+
+template <typename T, int B, int WARPS>
+cudaError_t configure_single() {
+    return cudaFuncSetAttribute(fsr_blocks_kernel<T, B, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SmemLayout<T>::bytes(WARPS));
+}
+
+template <typename T, int B, int WARPS>
+cudaError_t configure_batch() {
+    return cudaFuncSetAttribute(fsr_batch_kernel<T, B, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SmemLayout<T>::bytes(WARPS));
+}
+
+template <typename T, int B, int WARPS>
+cudaError_t launch_single_t(const KernelArgs& a, int sm_count, cudaStream_t stream) {
+    const size_t smem = SmemLayout<T>::bytes(WARPS);
+    int grid = 0;
+    cudaError_t e = persistent_grid(fsr_blocks_kernel<T, B, WARPS>, WARPS, smem, a.nblocks, sm_count, &grid);
+    if (e != cudaSuccess) return e;
+    fsr_blocks_kernel<T, B, WARPS><<<grid, WARPS * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int B, int WARPS>
+cudaError_t launch_batch_t(const BatchArgs& a, int sm_count, cudaStream_t stream) {
+    const size_t smem = SmemLayout<T>::bytes(WARPS);
+    int grid = 0;
+    cudaError_t e = persistent_grid(fsr_batch_kernel<T, B, WARPS>, WARPS, smem, a.total, sm_count, &grid);
+    if (e != cudaSuccess) return e;
+    fsr_batch_kernel<T, B, WARPS><<<grid, WARPS * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
 
 }  // namespace fsrk

@@ -29,7 +29,9 @@ PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG}
 
 # every function declared in include/fsr.h
 EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
-            "fsr_reconstruct_host", "fsr_num_blocks")
+            "fsr_reconstruct_host", "fsr_num_blocks", "fsr_reconstruct_batch",
+            "fsr_batch_create", "fsr_batch_launch", "fsr_batch_destroy",
+            "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule")
 
 
 class FsrError(RuntimeError):
@@ -39,7 +41,18 @@ class FsrError(RuntimeError):
 
 
 class fsr_config(ctypes.Structure):
-    _fields_ = [("device", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t)]
+    _fields_ = [("device", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
+                ("schedule_cache", ctypes.c_char_p)]
+
+
+class fsr_image_desc(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("height", ctypes.c_int), ("width", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("iters", ctypes.c_int), ("seq_out", ctypes.c_void_p)]
+
+
+class fsr_schedule(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int), ("chunk", ctypes.c_int)]
 
 
 class fsr_params(ctypes.Structure):
@@ -82,6 +95,19 @@ def load_library(path: str | None = None):
             f.restype = ip
         lib.fsr_num_blocks.argtypes = [ip, ip, ip]
         lib.fsr_num_blocks.restype = ctypes.c_longlong
+        dp, pp = ctypes.POINTER(fsr_image_desc), ctypes.POINTER(fsr_params)
+        lib.fsr_reconstruct_batch.argtypes = [vp, ip, dp, pp, vp]
+        lib.fsr_batch_create.argtypes = [vp, ip, dp, pp, ctypes.POINTER(vp)]
+        lib.fsr_batch_launch.argtypes = [vp, vp]
+        lib.fsr_batch_destroy.argtypes = [vp]
+        lib.fsr_autotune_batch.argtypes = [vp, ip, dp, pp, ctypes.POINTER(fsr_schedule),
+                                           ctypes.POINTER(ctypes.c_float)]
+        lib.fsr_get_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
+        lib.fsr_set_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
+        for name in ("fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
+                     "fsr_batch_destroy", "fsr_autotune_batch", "fsr_get_schedule",
+                     "fsr_set_schedule"):
+            getattr(lib, name).restype = ip
         if path is None:
             _lib = lib
         return lib
@@ -116,10 +142,11 @@ def fsr_last_error(handle=None) -> str:
     return load_library().fsr_last_error(handle).decode(errors="replace")
 
 
-def fsr_create(device: int = 0, workspace_bytes: int = 0) -> int:
+def fsr_create(device: int = 0, workspace_bytes: int = 0, schedule_cache: str | None = None) -> int:
     lib = load_library()
     h = ctypes.c_void_p()
-    _check(lib.fsr_create(ctypes.byref(fsr_config(int(device), int(workspace_bytes))),
+    cache = schedule_cache.encode() if schedule_cache else None
+    _check(lib.fsr_create(ctypes.byref(fsr_config(int(device), int(workspace_bytes), cache)),
                           ctypes.byref(h)), None)
     return h.value
 
@@ -178,12 +205,86 @@ def fsr_reconstruct_host(handle, img, mask, params: fsr_params, out, stream=None
                                                ctypes.byref(params), out.data_ptr(), stream), handle)
 
 
+def image_desc(img, mask, out, iters: int, seq_out=None) -> fsr_image_desc:
+    """Descriptor of one device image of a batch (torch CUDA tensors)."""
+    import torch
+    for t in (img, mask, out):
+        if not t.is_cuda:
+            raise ValueError("batch images must be CUDA tensors")
+    H, W, pitch = _geometry(img, mask, out)
+    seq_ptr = None
+    if seq_out is not None:
+        if not (seq_out.is_cuda and seq_out.dtype == torch.int16 and seq_out.is_contiguous()):
+            raise ValueError("seq_out must be a contiguous int16 CUDA tensor")
+        seq_ptr = seq_out.data_ptr()
+    return fsr_image_desc(img.data_ptr(), mask.data_ptr(), out.data_ptr(), H, W, pitch,
+                          int(iters), seq_ptr)
+
+
+def _descs(descs):
+    arr = (fsr_image_desc * len(descs))(*descs)
+    return arr, len(descs)
+
+
+def _stream_ptr(stream, device=None):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return stream
+
+
+def fsr_reconstruct_batch(handle, descs, params: fsr_params, stream=None) -> None:
+    arr, n = _descs(descs)
+    _check(load_library().fsr_reconstruct_batch(handle, n, arr, ctypes.byref(params),
+                                                _stream_ptr(stream)), handle)
+
+
+def fsr_batch_create(handle, descs, params: fsr_params) -> int:
+    arr, n = _descs(descs)
+    b = ctypes.c_void_p()
+    _check(load_library().fsr_batch_create(handle, n, arr, ctypes.byref(params), ctypes.byref(b)),
+           handle)
+    return b.value
+
+
+def fsr_batch_launch(batch, stream=None, handle=None) -> None:
+    _check(load_library().fsr_batch_launch(batch, _stream_ptr(stream)), handle)
+
+
+def fsr_batch_destroy(batch) -> None:
+    load_library().fsr_batch_destroy(batch)
+
+
+def fsr_autotune_batch(handle, descs, params: fsr_params):
+    arr, n = _descs(descs)
+    best = fsr_schedule()
+    ms = ctypes.c_float()
+    _check(load_library().fsr_autotune_batch(handle, n, arr, ctypes.byref(params),
+                                             ctypes.byref(best), ctypes.byref(ms)), handle)
+    return (best.warps, best.chunk), ms.value
+
+
+def fsr_get_schedule(handle, block: int = 4, precision: int = FSR_FP32):
+    s = fsr_schedule()
+    _check(load_library().fsr_get_schedule(handle, int(block), int(precision), ctypes.byref(s)),
+           handle)
+    return s.warps, s.chunk
+
+
+def fsr_set_schedule(handle, warps: int, chunk: int, block: int = 4, precision: int = FSR_FP32):
+    s = fsr_schedule(int(warps), int(chunk))
+    _check(load_library().fsr_set_schedule(handle, int(block), int(precision), ctypes.byref(s)),
+           handle)
+
+
 class Handle:
     """Owning wrapper of an ``fsr_handle``."""
 
-    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+    def __init__(self, device: int = 0, workspace_bytes: int = 0, schedule_cache: str | None = None):
         self.device = device
-        self.ptr = fsr_create(device, workspace_bytes)
+        self.ptr = fsr_create(device, workspace_bytes, schedule_cache)
 
     def close(self):
         if self.ptr:
