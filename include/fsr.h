@@ -182,6 +182,36 @@ int fsr_autotune_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_
 int fsr_get_schedule(const fsr_handle *h, int block, int precision, fsr_schedule *out);
 int fsr_set_schedule(fsr_handle *h, int block, int precision, const fsr_schedule *s);
 
+/* ---- Batch form without device allocation -------------------------------
+ * The paper has no counterpart of this entry point: it exists for callers
+ * that may not allocate device memory, e.g. code running under a framework
+ * whose allocator owns the whole device-memory budget, real-time loops that
+ * cannot afford an allocation (cudaMalloc may synchronise the device and stall
+ * other streams), or plug-ins that may not keep device memory between calls.
+ *
+ * Same work as fsr_reconstruct_batch on the calling thread's current device,
+ * with the default schedule, but with no handle and no allocation: the work
+ * table (counter, block prefix sums, per-image arguments) lives in a fixed
+ * FSR_STATIC_SCRATCH_BYTES array of the library's static device memory, which
+ * every device that loads the library holds until the process exits.
+ *   - At most FSR_STATIC_MAX_IMAGES images per call; larger batches are
+ *     rejected with FSR_ERR_INVALID_ARG and a message.
+ *   - The first call on a device does a one-time set-up there (finds the
+ *     array's device address, sets the kernels' shared-memory limits); make
+ *     that first call before any stream capture.
+ *   - Every call shares the one array per device and overwrites it (the work
+ *     counter is reset by each call's table upload): calls whose work overlaps
+ *     on the device race and give wrong results.  Keep them on one stream, or
+ *     wait for one to finish before the next starts.
+ *   - The table is uploaded from host memory of the library, consumed before
+ *     the call returns; the call is otherwise asynchronous on `stream`.
+ *   - err/err_len: optional buffer for the text of an error (may be NULL).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, as for fsr_reconstruct_batch. */
+#define FSR_STATIC_MAX_IMAGES 64
+#define FSR_STATIC_SCRATCH_BYTES 8192
+int fsr_reconstruct_batch_static(int n, const fsr_image_desc *d, const fsr_params *p, void *stream,
+                                 char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

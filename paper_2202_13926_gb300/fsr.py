@@ -31,7 +31,8 @@ PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG}
 EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
             "fsr_reconstruct_host", "fsr_num_blocks", "fsr_reconstruct_batch",
             "fsr_batch_create", "fsr_batch_launch", "fsr_batch_destroy",
-            "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule")
+            "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule",
+            "fsr_reconstruct_batch_static")
 
 
 class FsrError(RuntimeError):
@@ -104,7 +105,8 @@ def load_library(path: str | None = None):
                                            ctypes.POINTER(ctypes.c_float)]
         lib.fsr_get_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
         lib.fsr_set_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
-        for name in ("fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
+        lib.fsr_reconstruct_batch_static.argtypes = [ip, dp, pp, vp, ctypes.c_char_p, ctypes.c_size_t]
+        for name in ("fsr_reconstruct_batch_static", "fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
                      "fsr_batch_destroy", "fsr_autotune_batch", "fsr_get_schedule",
                      "fsr_set_schedule"):
             getattr(lib, name).restype = ip
@@ -239,6 +241,17 @@ def fsr_reconstruct_batch(handle, descs, params: fsr_params, stream=None) -> Non
     arr, n = _descs(descs)
     _check(load_library().fsr_reconstruct_batch(handle, n, arr, ctypes.byref(params),
                                                 _stream_ptr(stream)), handle)
+
+
+def fsr_reconstruct_batch_static(descs, params: fsr_params, stream=None) -> None:
+    """Batch reconstruction that allocates no device memory (scratch in the
+    library's static device array; at most 64 images per call)."""
+    arr, n = _descs(descs)
+    buf = ctypes.create_string_buffer(512)
+    code = load_library().fsr_reconstruct_batch_static(n, arr, ctypes.byref(params),
+                                                       _stream_ptr(stream), buf, len(buf))
+    if code != FSR_OK:
+        raise FsrError(code, buf.value.decode(errors="replace"))
 
 
 def fsr_batch_create(handle, descs, params: fsr_params) -> int:
