@@ -182,6 +182,57 @@ int fsr_autotune_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_
 int fsr_get_schedule(const fsr_handle *h, int block, int precision, fsr_schedule *out);
 int fsr_set_schedule(fsr_handle *h, int block, int precision, const fsr_schedule *s);
 
+/* ---- Serving form: continuous batching of a request stream --------------
+ * A server owns a device-memory pool of a fixed budget and a worker thread.
+ * fsr_server_submit queues a request (HOST buffers) and returns at once.  The
+ * worker admits queued requests in arrival order while the pool has room for
+ * their image, mask and output and a slot is free, starts their host-to-device
+ * copies, and launches every admitted, not yet launched request together as
+ * one batch (fsr_reconstruct_batch's kernel) on the next of its compute
+ * streams: requests that arrive while others run join the next launch, and
+ * launches, copies in and copies out of different requests overlap on the
+ * device.  A finished request's output is copied back to its host buffer, its
+ * pool memory is released, and its latency (submit to output on the host) is
+ * recorded.  Results do not depend on what else is in flight: every block is
+ * computed by one warp with the arithmetic of fsr_reconstruct. */
+
+typedef struct fsr_server fsr_server;
+
+typedef struct fsr_server_config {
+    size_t pool_bytes;   /* device-memory budget of in-flight requests (image, mask,
+                            output and launch tables), allocated once at creation */
+    int max_inflight;    /* admitted requests at most (slots), >= 1 */
+    int streams;         /* compute streams launches rotate over, 1..8 */
+} fsr_server_config;
+
+/* Create a server on the handle's device; p gives B, L, rho, gamma,
+ * freq_weight and precision for every request (p->iters, p->seq_out ignored).
+ * Errors: INVALID_ARG, OOM (the pool cannot be allocated), CUDA. */
+int fsr_server_create(fsr_handle *h, const fsr_server_config *cfg, const fsr_params *p, fsr_server **out);
+
+/* Queue one request.  img/mask/out are HOST buffers, tightly packed
+ * (pitch = width), owned by the caller and left untouched by the caller until
+ * the request completes (pinned memory lets the copies overlap compute).
+ * *ticket receives the request's id (0, 1, 2, ... in submission order).
+ * Errors: INVALID_ARG (bad sizes, or a request larger than the whole pool). */
+int fsr_server_submit(fsr_server *s, const float *img, const uint8_t *mask, int height, int width, int iters,
+                      float *out, long long *ticket);
+
+/* Completed requests since the last call, in completion order: up to `max`
+ * tickets and their latencies in milliseconds; *n receives the count.
+ * With wait_ms > 0 the call blocks up to that long for at least one.
+ * A request whose device work failed is reported with latency -1. */
+int fsr_server_poll(fsr_server *s, long long *tickets, double *latency_ms, int max, int *n, int wait_ms);
+
+/* Counters: submitted, completed, requests currently queued and admitted,
+ * launches issued, peak pool bytes in use.  Any pointer may be NULL. */
+int fsr_server_stats(const fsr_server *s, long long *submitted, long long *completed, int *queued,
+                     int *inflight, long long *launches, size_t *peak_pool_bytes);
+
+/* Stop accepting work, finish everything admitted or queued, release the
+ * pool and streams.  NULL is accepted. */
+int fsr_server_destroy(fsr_server *s);
+
 /* ---- Batch form without device allocation -------------------------------
  * The paper has no counterpart of this entry point: it exists for callers
  * that may not allocate device memory, e.g. code running under a framework

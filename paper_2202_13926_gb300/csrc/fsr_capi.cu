@@ -13,36 +13,8 @@
 #include <vector>
 
 #include "fsr.h"
+#include "fsr_internal.h"
 #include "fsr_launch.h"
-
-namespace {
-
-constexpr int kNumB = 4;   // B in {2, 4, 8, 16}
-int b_index(int B) { return B == 2 ? 0 : B == 4 ? 1 : B == 8 ? 2 : B == 16 ? 3 : -1; }
-
-}  // namespace
-
-struct fsr_handle {
-    int device = 0;
-    int sm_count = 0;
-    char device_name[256] = {0};
-    size_t ws_cap = 0;       // 0 = no cap
-    size_t ws_used = 0;
-    char err[512] = {0};
-    std::string cache_path;
-    // batch schedules per [precision][B]
-    fsrk::Schedule sched[2][kNumB] = {{{12, 1}, {12, 1}, {12, 1}, {12, 1}}, {{4, 1}, {4, 1}, {4, 1}, {4, 1}}};
-    // device staging buffers of fsr_reconstruct_host
-    float* d_img = nullptr;
-    uint8_t* d_mask = nullptr;
-    float* d_out = nullptr;
-    size_t stage_pixels = 0;
-    // work table of the one-shot batch entry point
-    void* d_table = nullptr;
-    void* h_table = nullptr;       // pinned host staging of the table
-    size_t table_bytes = 0;
-    cudaEvent_t table_free = nullptr;
-};
 
 struct fsr_batch {
     fsr_handle* h = nullptr;
@@ -53,8 +25,10 @@ struct fsr_batch {
 };
 
 namespace {
-
 thread_local char g_create_err[512] = {0};
+}  // namespace
+
+namespace fsri {
 
 int fail(fsr_handle* h, int code, const char* fmt, ...) {
     char* buf = h ? h->err : g_create_err;
@@ -225,6 +199,11 @@ cudaError_t launch_batch(const fsrk::BatchArgs& a, const fsr_params* p, fsrk::Sc
     return (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(a, p->block, sc, sm_count, s)
                                              : fsrk::launch_batch_fp32(a, p->block, sc, sm_count, s);
 }
+
+}  // namespace fsri
+
+namespace {
+using namespace fsri;
 
 bool schedule_ok(int precision, int B, const fsrk::Schedule& s) {
     return s.chunk >= 1 && s.chunk <= 64 && fsrk::batch_schedule_supported(precision == FSR_FP64_DEBUG, B, s.warps);

@@ -32,7 +32,8 @@ EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
             "fsr_reconstruct_host", "fsr_num_blocks", "fsr_reconstruct_batch",
             "fsr_batch_create", "fsr_batch_launch", "fsr_batch_destroy",
             "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule",
-            "fsr_reconstruct_batch_static")
+            "fsr_reconstruct_batch_static", "fsr_server_create", "fsr_server_submit",
+            "fsr_server_poll", "fsr_server_stats", "fsr_server_destroy")
 
 
 class FsrError(RuntimeError):
@@ -54,6 +55,11 @@ class fsr_image_desc(ctypes.Structure):
 
 class fsr_schedule(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int), ("chunk", ctypes.c_int)]
+
+
+class fsr_server_config(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 class fsr_params(ctypes.Structure):
@@ -106,6 +112,17 @@ def load_library(path: str | None = None):
         lib.fsr_get_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
         lib.fsr_set_schedule.argtypes = [vp, ip, ip, ctypes.POINTER(fsr_schedule)]
         lib.fsr_reconstruct_batch_static.argtypes = [ip, dp, pp, vp, ctypes.c_char_p, ctypes.c_size_t]
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        lib.fsr_server_create.argtypes = [vp, ctypes.POINTER(fsr_server_config), pp, ctypes.POINTER(vp)]
+        lib.fsr_server_submit.argtypes = [vp, vp, vp, ip, ip, ip, vp, llp]
+        lib.fsr_server_poll.argtypes = [vp, llp, ctypes.POINTER(ctypes.c_double), ip,
+                                        ctypes.POINTER(ctypes.c_int), ip]
+        lib.fsr_server_stats.argtypes = [vp, llp, llp, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), llp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.fsr_server_destroy.argtypes = [vp]
+        for name in ("fsr_server_create", "fsr_server_submit", "fsr_server_poll",
+                     "fsr_server_stats", "fsr_server_destroy"):
+            getattr(lib, name).restype = ip
         for name in ("fsr_reconstruct_batch_static", "fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
                      "fsr_batch_destroy", "fsr_autotune_batch", "fsr_get_schedule",
                      "fsr_set_schedule"):
@@ -329,3 +346,96 @@ class Handle:
             out = np.empty(img.shape, np.float32)
         fsr_reconstruct_host(self.ptr, img, mask, make_params(**kw), out, stream)
         return out
+
+
+# ---- serving form ------------------------------------------------------------
+
+def fsr_server_create(handle, pool_bytes: int, max_inflight: int, streams: int,
+                      params: fsr_params) -> int:
+    srv = ctypes.c_void_p()
+    cfg = fsr_server_config(int(pool_bytes), int(max_inflight), int(streams))
+    _check(load_library().fsr_server_create(handle, ctypes.byref(cfg), ctypes.byref(params),
+                                            ctypes.byref(srv)), handle)
+    return srv.value
+
+
+def fsr_server_submit(server, img_ptr: int, mask_ptr: int, height: int, width: int, iters: int,
+                      out_ptr: int, handle=None) -> int:
+    t = ctypes.c_longlong()
+    _check(load_library().fsr_server_submit(server, img_ptr, mask_ptr, int(height), int(width),
+                                            int(iters), out_ptr, ctypes.byref(t)), handle)
+    return t.value
+
+
+def fsr_server_poll(server, max_items: int = 256, wait_ms: int = 0):
+    tk = (ctypes.c_longlong * max_items)()
+    lat = (ctypes.c_double * max_items)()
+    n = ctypes.c_int()
+    _check(load_library().fsr_server_poll(server, tk, lat, int(max_items), ctypes.byref(n),
+                                          int(wait_ms)), None)
+    return [(tk[i], lat[i]) for i in range(n.value)]
+
+
+def fsr_server_stats(server) -> dict:
+    sub, com, lau = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    q, inf = ctypes.c_int(), ctypes.c_int()
+    peak = ctypes.c_size_t()
+    _check(load_library().fsr_server_stats(server, ctypes.byref(sub), ctypes.byref(com),
+                                           ctypes.byref(q), ctypes.byref(inf), ctypes.byref(lau),
+                                           ctypes.byref(peak)), None)
+    return dict(submitted=sub.value, completed=com.value, queued=q.value, inflight=inf.value,
+                launches=lau.value, peak_pool_bytes=peak.value)
+
+
+def fsr_server_destroy(server) -> None:
+    load_library().fsr_server_destroy(server)
+
+
+class Server:
+    """Owning wrapper of an ``fsr_server``.  Requests take host tensors
+    (float32 image, uint8 mask; pinned for overlapped copies); the wrapper
+    keeps them alive until the request completes and returns its output."""
+
+    def __init__(self, handle: "Handle", pool_bytes: int, max_inflight: int = 64, streams: int = 2,
+                 **params):
+        self.handle = handle
+        self.ptr = fsr_server_create(handle.ptr, pool_bytes, max_inflight, streams,
+                                     make_params(**params))
+        self.live = {}
+
+    def submit(self, img, mask, iters: int, out=None) -> int:
+        import torch
+        if out is None:
+            out = torch.empty(img.shape, dtype=torch.float32, pin_memory=img.is_pinned())
+        for t in (img, mask, out):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("server requests take contiguous host tensors")
+        if img.dtype != torch.float32 or mask.dtype != torch.uint8 or out.dtype != torch.float32:
+            raise ValueError("img/out float32, mask uint8")
+        H, W = img.shape
+        t = fsr_server_submit(self.ptr, img.data_ptr(), mask.data_ptr(), H, W, iters, out.data_ptr(),
+                              self.handle.ptr)
+        self.live[t] = (img, mask, out)
+        return t
+
+    def poll(self, wait_ms: int = 0):
+        """[(ticket, latency_ms, output tensor)] of the requests completed since the last poll."""
+        res = []
+        for t, lat in fsr_server_poll(self.ptr, 1024, wait_ms):
+            img, mask, out = self.live.pop(t)
+            res.append((t, lat, out))
+        return res
+
+    def stats(self) -> dict:
+        return fsr_server_stats(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            fsr_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
