@@ -199,6 +199,76 @@ def run_reference(args, rank, world):
     _barrier(dist)
 
 
+def _measure_batch(fsr, handle, dev, torch):
+    """48 images of mixed size/mask/K in one graph-captured persistent launch."""
+    from paper_2202_13926_gb300 import synth
+    items = synth.batch_case()
+    descs = []
+    for it in items:
+        it["d_img"] = torch.from_numpy(it["img"]).to(dev)
+        it["d_mask"] = torch.from_numpy(it["mask"]).to(dev)
+        it["d_out"] = torch.empty_like(it["d_img"])
+        descs.append(fsr.image_desc(it["d_img"], it["d_mask"], it["d_out"], it["K"]))
+    params = fsr.make_params(block=B, border=L, rho=RHO, gamma=GAMMA)
+    # schedule autotuned on the 24 smaller images (same K mix), then applied to all 48
+    small = sorted(range(len(items)), key=lambda i: items[i]["img"].size)[:24]
+    (warps, chunk), _ = fsr.fsr_autotune_batch(handle.ptr, [descs[i] for i in small], params)
+    plan = fsr.fsr_batch_create(handle.ptr, descs, params)
+    stream = torch.cuda.current_stream(dev)
+    try:
+        fsr.fsr_batch_launch(plan, stream, handle.ptr)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record(stream)
+        for _ in range(reps):
+            fsr.fsr_batch_launch(plan, stream, handle.ptr)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+    finally:
+        fsr.fsr_batch_destroy(plan)
+    mp = sum(it["img"].size for it in items) / 1e6
+    biters = sum(fsr.fsr_num_blocks(*it["img"].shape, B) * it["K"] for it in items)
+    return {"workload": "48 images: 12 each of 256x256, 1280x720, 1920x1080, 3840x2160; "
+                        "i.i.d. 10-90% or 16x16 macroblock 5-20% loss; K in {50,100,200}",
+            "ms_per_batch": ms, "mp_per_s": mp / (ms / 1e3),
+            "block_iterations_per_s": biters / (ms / 1e3),
+            "schedule": {"warps": warps, "chunk": chunk, "tuned_on": "the 24 smaller images"},
+            "graph": True}
+
+
+def _measure_serving(fsr, handle, torch, seconds: float):
+    """Poisson stream, mean 120 req/s: 720p/1080p/4K frames, quarter sampling or
+    macroblock loss, K in {50, 100}, through the continuous-batching server."""
+    from paper_2202_13926_gb300 import serving, synth
+    sizes = [("720p", 720, 1280), ("1080p", 1080, 1920), ("4K", 2160, 3840)]
+    frames, names, mps, cls = [], [], [], []
+    for ci, (name, hh, ww) in enumerate(sizes):
+        for mk in ("quarter", "macroblock"):
+            img = synth.pink_image(hh, ww, 100 + ci)
+            mask = synth.quarter_mask(hh, ww, 200 + ci) if mk == "quarter" else \
+                synth.macroblock_mask(hh, ww, 300 + ci, 0.12)
+            frames.append((torch.from_numpy(img).pin_memory(), torch.from_numpy(mask).pin_memory()))
+            mps.append(hh * ww / 1e6)
+            cls.append(ci)
+    arr = serving.poisson_arrivals(120.0, seconds, seed=9)
+    rng = np.random.default_rng(10)
+    kinds = rng.integers(0, len(frames), arr.size)
+    iters = rng.choice([50, 100], arr.size)
+    with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=2,
+                    block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
+        res = serving.run_stream(srv, frames, arr, kinds, iters)
+        st = srv.stats()
+    res["kinds"] = np.asarray([cls[k] for k in kinds])
+    summ = serving.summarize(res, [n for n, _, _ in sizes], {i: mps[2 * i] for i in range(3)})
+    summ.update({"rate_hz": 120.0, "duration_s": seconds, "launches": st["launches"],
+                 "peak_pool_bytes": st["peak_pool_bytes"], "frame_period_ms": 1000.0 / 60.0,
+                 "workload": "Poisson arrivals, 720p/1080p/4K x quarter/macroblock masks, K in {50,100}"})
+    return summ
+
+
 def _config():
     return {"workload": "fsr_1080p_quarter_sampling_K100",
             "image": f"{W}x{H} float32, seeded 1/f^2 noise + edges (seed {IMG_SEED})",
@@ -216,6 +286,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 48-image batch measurement")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="length of the Poisson serving stream (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _dist_env()
@@ -329,6 +402,11 @@ def main():
         "clocks": clocks,
         "device": {"name": props.name, "sm_count": n_sm},
     }
+
+    if world == 1 and not args.no_batch:
+        line["batch"] = _measure_batch(fsr, handle, dev, torch)
+    if world == 1 and args.serve_seconds > 0:
+        line["serving"] = _measure_serving(fsr, handle, torch, args.serve_seconds)
 
     if world == 1 and not args.no_cpu_baseline:
         import oracle
