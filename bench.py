@@ -432,6 +432,26 @@ def main():
                           "psnr_gpu_db": psnr(got), "psnr_oracle_db": psnr(ref),
                           "dpsnr_db": dpsnr, "pass": bool(frac >= 0.999 and dpsnr <= 0.01),
                           "blocks_checked": int(len(ids))}
+        # precision study: forward transform on tensor cores, same sample
+        study = {}
+        for mode in ("fp32", "tc_bf16x3", "tc_tf32"):
+            pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, precision=mode)
+            for _ in range(2):
+                fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+            ta = torch.cuda.Event(enable_timing=True)
+            tb = torch.cuda.Event(enable_timing=True)
+            ta.record(stream)
+            for _ in range(5):
+                fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+            tb.record(stream)
+            torch.cuda.synchronize(dev)
+            o = d_out.cpu().numpy()
+            g = np.stack([o[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+            dd = np.abs(g.astype(np.float64) - ref)
+            study[mode] = {"ms_per_frame": ta.elapsed_time(tb) / 5, "psnr_db": psnr(g),
+                           "dpsnr_vs_oracle_db": psnr(g) - psnr(ref), "max_abs_vs_oracle": float(dd.max()),
+                           "frac_within_0.5": float(np.mean(dd <= 0.5))}
+        line["precision_study"] = study
     print(json.dumps(line), flush=True)
     handle.close()
 

@@ -51,6 +51,10 @@ extern "C" {
 /* Arithmetic of the iteration (fsr_params.precision). */
 #define FSR_FP32       0  /* FP32 everywhere (the production path) */
 #define FSR_FP64_DEBUG 1  /* FP64 everywhere; selection sequences comparable with an FP64 reference */
+/* Precision study (single-image entry points, B = 4): the forward 2-D DFT of
+ * a3 on tensor cores with FP32 accumulation, the iteration in FP32. */
+#define FSR_TC_BF16X3  2  /* operands split into BF16 hi + lo, products hi.hi + hi.lo + lo.hi */
+#define FSR_TC_TF32    3  /* operands rounded to TF32 */
 
 /* Library configuration (fsr_create). */
 typedef struct fsr_config {
@@ -68,7 +72,7 @@ typedef struct fsr_params {
     float rho;        /* rho-hat of Eq. (5), in (0, 1] */
     float gamma;      /* gamma of Eqs. (11)-(12), in (0, 1] */
     int freq_weight;  /* 1: objective w_f |R_w|^2 (Eq. 8, paper default); 0: |R_w|^2 */
-    int precision;    /* FSR_FP32 or FSR_FP64_DEBUG */
+    int precision;    /* FSR_FP32, FSR_FP64_DEBUG, or (single image, B = 4) FSR_TC_BF16X3 / FSR_TC_TF32 */
     int16_t *seq_out; /* optional DEVICE buffer of N*K entries (N = number of blocks,
                          block b = by*ceil(width/B) + bx): the selected u*S+v of each
                          iteration, -1 for a block without known pixels; NULL = off */

@@ -175,6 +175,213 @@ __device__ __forceinline__ double warp_max(double x) {
     return x;
 }
 
+// ---------------------------------------------------------------- forward
+// transform on tensor cores (precision study).  Both passes of the 2-D DFT
+// are one real GEMM  D (32 x 64) = A (32 x 64) . M (64 x 64)  with
+//   A = [Re | Im] of the 32 x 32 complex input (rows m, columns n),
+//   M = [[Fr, Fi], [-Fi, Fr]],  F[n][l] = e^{-j 2 pi n l / 32} (symmetric),
+// so D = [Re | Im] of (input . F).  Pass 1 gives Y = z F (DFT over n); pass
+// 2 takes A = Y^T and gives Z^T = Y^T F, i.e. Z = F Y F (DFT over both axes).
+// Operands are rounded to TF32, or split into BF16 hi + lo with the three
+// products hi.hi + hi.lo + lo.hi; accumulation is FP32.
+enum class Dft { SIMT = 0, TF32 = 1, BF16X3 = 2 };
+
+constexpr int TC_AS = 68;   // row stride (floats) of A and of M^T in TF32 form
+constexpr int TC_HS = 72;   // row stride (bf16 elements) of the BF16 hi/lo arrays
+
+template <Dft D> struct TcTable;
+template <> struct TcTable<Dft::SIMT> { static constexpr size_t bytes = 0; };
+template <> struct TcTable<Dft::TF32> { static constexpr size_t bytes = sizeof(float) * 64 * TC_AS; };
+template <> struct TcTable<Dft::BF16X3> { static constexpr size_t bytes = 2 * sizeof(uint16_t) * 64 * TC_HS; };
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    uint16_t r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float bf16_value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// M^T (n-major: row = output column nn, column = inner index kk) of the
+// real-expanded DFT matrix, per CTA.
+template <Dft D>
+__device__ __forceinline__ void tc_table(unsigned char* tab) {
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int nn = i / 64, kk = i % 64;
+        const int n = kk & 31, l = nn & 31, t = (n * l) & 31;
+        const float c = (float)cos_2pi32(t), sn = (float)sin_2pi32(t);
+        // M[kk][nn]: [[cos, -sin], [sin, cos]]
+        const float v = (kk < 32) ? ((nn < 32) ? c : -sn) : ((nn < 32) ? sn : c);
+        if (D == Dft::TF32) {
+            reinterpret_cast<uint32_t*>(tab)[nn * TC_AS + kk] = tf32_bits(v);
+        } else if (D == Dft::BF16X3) {
+            uint16_t* hi = reinterpret_cast<uint16_t*>(tab);
+            uint16_t* lo = hi + 64 * TC_HS;
+            const uint16_t h = bf16_bits(v);
+            hi[nn * TC_HS + kk] = h;
+            lo[nn * TC_HS + kk] = bf16_bits(v - bf16_value(h));
+        }
+    }
+}
+
+// Stage the 32 x 64 operand A = [re | im] of this warp's block in shared
+// memory (rows r, re at column c, im at column 32 + c), in the GEMM's format.
+template <Dft D>
+__device__ __forceinline__ void tc_put(unsigned char* buf, int r, int c, float re, float im) {
+    if (D == Dft::TF32) {
+        uint32_t* a = reinterpret_cast<uint32_t*>(buf);
+        a[r * TC_AS + c] = tf32_bits(re);
+        a[r * TC_AS + 32 + c] = tf32_bits(im);
+    } else {
+        uint16_t* hi = reinterpret_cast<uint16_t*>(buf);
+        uint16_t* lo = hi + 32 * TC_HS;
+        const uint16_t hr = bf16_bits(re), hm = bf16_bits(im);
+        hi[r * TC_HS + c] = hr;
+        hi[r * TC_HS + 32 + c] = hm;
+        lo[r * TC_HS + c] = bf16_bits(re - bf16_value(hr));
+        lo[r * TC_HS + 32 + c] = bf16_bits(im - bf16_value(hm));
+    }
+}
+
+// D = A . M for this warp; acc[mt][nt][i] is row 16 mt + gid (+8 for i >= 2),
+// column 8 nt + 2 tig (+1 for odd i).
+template <Dft D>
+__device__ __forceinline__ void tc_gemm(const unsigned char* buf, const unsigned char* tab, int lane,
+                                        float (&acc)[2][8][4]) {
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+    if (D == Dft::TF32) {
+        const uint32_t* A = reinterpret_cast<const uint32_t*>(buf);
+        const uint32_t* Bt = reinterpret_cast<const uint32_t*>(tab);
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+            const int k0 = 8 * ks;
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = 16 * mt + gid;
+                a[mt][0] = A[r * TC_AS + k0 + tig];
+                a[mt][1] = A[(r + 8) * TC_AS + k0 + tig];
+                a[mt][2] = A[r * TC_AS + k0 + tig + 4];
+                a[mt][3] = A[(r + 8) * TC_AS + k0 + tig + 4];
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint32_t b0 = Bt[(8 * nt + gid) * TC_AS + k0 + tig];
+                const uint32_t b1 = Bt[(8 * nt + gid) * TC_AS + k0 + tig + 4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][nt], a[mt], b0, b1);
+            }
+        }
+    } else {
+        const uint16_t* Ahi = reinterpret_cast<const uint16_t*>(buf);
+        const uint16_t* Alo = Ahi + 32 * TC_HS;
+        const uint16_t* Bhi = reinterpret_cast<const uint16_t*>(tab);
+        const uint16_t* Blo = Bhi + 64 * TC_HS;
+        auto pair = [](const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); };
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            const int k0 = 16 * ks;
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = 16 * mt + gid;
+                ah[mt][0] = pair(Ahi + r * TC_HS + k0 + 2 * tig);
+                ah[mt][1] = pair(Ahi + (r + 8) * TC_HS + k0 + 2 * tig);
+                ah[mt][2] = pair(Ahi + r * TC_HS + k0 + 2 * tig + 8);
+                ah[mt][3] = pair(Ahi + (r + 8) * TC_HS + k0 + 2 * tig + 8);
+                al[mt][0] = pair(Alo + r * TC_HS + k0 + 2 * tig);
+                al[mt][1] = pair(Alo + (r + 8) * TC_HS + k0 + 2 * tig);
+                al[mt][2] = pair(Alo + r * TC_HS + k0 + 2 * tig + 8);
+                al[mt][3] = pair(Alo + (r + 8) * TC_HS + k0 + 2 * tig + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = (8 * nt + gid) * TC_HS + k0 + 2 * tig;
+                const uint32_t bh0 = pair(Bhi + col), bh1 = pair(Bhi + col + 8);
+                const uint32_t bl0 = pair(Blo + col), bl1 = pair(Blo + col + 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(acc[mt][nt], al[mt], bh0, bh1);
+                    mma_bf16(acc[mt][nt], ah[mt], bl0, bl1);
+                    mma_bf16(acc[mt][nt], ah[mt], bh0, bh1);
+                }
+            }
+        }
+    }
+}
+
+// Forward 2-D DFT of z = zr + j zi (lane n holds column n) on tensor cores;
+// on return lane k holds Z[k][0..31].  buf: this warp's scratch (>= 9.2 KB).
+template <Dft D>
+__device__ __forceinline__ void tc_dft2(float (&zr)[S], float (&zi)[S], unsigned char* buf,
+                                        const unsigned char* tab, int lane) {
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][8][4];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < S; ++m) tc_put<D>(buf, m, lane, zr[m], zi[m]);   // A[m][n] = z[m][n]
+    __syncwarp();
+    tc_gemm<D>(buf, tab, lane, acc);                                     // [Yr | Yi], Y = z F
+    __syncwarp();
+    // A2 = Y^T: row l, column m
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m = 16 * mt + gid + ((i & 2) ? 8 : 0);
+                const int l = 8 * nt + 2 * tig + (i & 1);
+                tc_put<D>(buf, l, m, acc[mt][nt][i], acc[mt][nt + 4][i]);
+            }
+    __syncwarp();
+    tc_gemm<D>(buf, tab, lane, acc);                                     // [Re | Im] of Z^T
+    __syncwarp();
+    // Z[k][l] = D2[l][k] (re), D2[l][32 + k] (im): row k of Z to lane k
+    float2* zb = reinterpret_cast<float2*>(buf);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int l = 16 * mt + gid + ((i & 2) ? 8 : 0);
+                const int k = 8 * nt + 2 * tig + (i & 1);
+                zb[k * TSTRIDE + l] = make_float2(acc[mt][nt][i], acc[mt][nt + 4][i]);
+            }
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+        const float2 v = zb[lane * TSTRIDE + l];
+        zr[l] = v.x;
+        zi[l] = v.y;
+    }
+    __syncwarp();
+}
+
 // Row stride (in complex elements) of the doubled W rows: 64 entries + pad,
 // chosen so that 32 lanes reading 32 different rows at one column hit
 // distinct banks (128-bit loads for FP32, 128-bit elements for FP64).
@@ -210,10 +417,10 @@ struct BlockState {
 // a1-a3: load the support (lane n = column n), weight it, transform it.
 // On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
 // row k in zr/zi and every row of W is in Wd twice in a row.
-template <typename T, int WS>
+template <typename T, int WS, Dft DFT>
 __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
                                               const T* __restrict__ sw0,
-                                              typename Vec2<T>::type* Wd,
+                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
                                               T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
     using T2 = typename Vec2<T>::type;
     const int xc = x0 + lane;
@@ -267,25 +474,30 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
 #pragma unroll
     for (int m = 0; m < S; ++m) zi[m] = zi[m] * alpha;
 
-    // a3: FFT over m (lane n holds column n)
-    fft32<T>(zr, zi);
-    // transpose through this warp's (not yet used) W area
-    T2* tb = Wd;
-    __syncwarp();
+    if constexpr (DFT != Dft::SIMT) {
+        // a3 on tensor cores (precision study); lane k ends with Z[k][0..31]
+        tc_dft2<DFT>(zr, zi, reinterpret_cast<unsigned char*>(Wd), tctab, lane);
+    } else {
+        // a3: FFT over m (lane n holds column n)
+        fft32<T>(zr, zi);
+        // transpose through this warp's (not yet used) W area
+        T2* tb = Wd;
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-        T2 v; v.x = zr[k]; v.y = zi[k];
-        tb[k * TSTRIDE + lane] = v;
-    }
-    __syncwarp();
+        for (int k = 0; k < S; ++k) {
+            T2 v; v.x = zr[k]; v.y = zi[k];
+            tb[k * TSTRIDE + lane] = v;
+        }
+        __syncwarp();
 #pragma unroll
-    for (int n = 0; n < S; ++n) {
-        const T2 v = tb[lane * TSTRIDE + n];
-        zr[n] = v.x; zi[n] = v.y;
+        for (int n = 0; n < S; ++n) {
+            const T2 v = tb[lane * TSTRIDE + n];
+            zr[n] = v.x; zi[n] = v.y;
+        }
+        __syncwarp();
+        // FFT over n: lane k holds Z[k][0..31]
+        fft32<T>(zr, zi);
     }
-    __syncwarp();
-    // FFT over n: lane k holds Z[k][0..31]
-    fft32<T>(zr, zi);
 
     // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,  W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha)
     const int src = (S - lane) & (S - 1);
@@ -621,11 +833,11 @@ __device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf
 }
 
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
-template <typename T, int B>
+template <typename T, int B, Dft DFT = Dft::SIMT>
 __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
-                                              int lane) {
+                                              const unsigned char* tctab, int lane) {
     constexpr int P = TargetPix<B>::P;
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -638,7 +850,7 @@ __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk
     for (int q = 0; q < P; ++q) gacc[q] = T(0);
 
     int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
-    if (prepare_block<T, SmemLayout<T>::WS>(im, y0, x0, lane, sw0, Wd, zr, zi, st)) {
+    if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, zr, zi, st)) {
         iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
         __syncwarp();   // W area free for the next block
     } else if (seq != nullptr && lane == 0) {
@@ -665,7 +877,7 @@ __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk
 template <typename T, int WARPS> struct MinBlocks { static constexpr int value = 1; };
 template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value = 12 / WARPS; };
 
-template <typename T, int B, int WARPS>
+template <typename T, int B, int WARPS, Dft DFT = Dft::SIMT>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
 fsr_blocks_kernel(const KernelArgs a) {
     using T2 = typename Vec2<T>::type;
@@ -679,13 +891,15 @@ fsr_blocks_kernel(const KernelArgs a) {
     T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
     T2* rowbuf = Wd + Lay::w_elems;
 
+    unsigned char* tctab = smem + Lay::bytes(WARPS);   // tensor-core DFT table (precision study)
     cta_tables<T>(a.mth, sw0, swf, scs);
+    if constexpr (DFT != Dft::SIMT) tc_table<DFT>(tctab);
     __syncthreads();
 
     const T gamma = T(a.mth.gamma);
     for (long long blk = (long long)blockIdx.x * WARPS + warp; blk < a.nblocks;
          blk += (long long)gridDim.x * WARPS)
-        process_block<T, B>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, lane);
+        process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, lane);
 }
 
 // Batch form: every warp takes `chunk` consecutive entries of the block list
@@ -724,7 +938,7 @@ fsr_batch_kernel(const BatchArgs a) {
             }
             const ImageArgs im = a.images[lo];
             process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
-                                rowbuf, lane);
+                                rowbuf, nullptr, lane);
         }
     }
 }

@@ -78,8 +78,11 @@ int check_method(fsr_handle* h, const fsr_params* p) {
     if (!(p->rho > 0.f && p->rho <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "rho must be in (0, 1]");
     if (!(p->gamma > 0.f && p->gamma <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "gamma must be in (0, 1]");
     if (p->freq_weight != 0 && p->freq_weight != 1) return fail(h, FSR_ERR_INVALID_ARG, "freq_weight must be 0 or 1");
-    if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
+    if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG && p->precision != FSR_TC_BF16X3 &&
+        p->precision != FSR_TC_TF32)
         return fail(h, FSR_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
+    if ((p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32) && p->block != 4)
+        return fail(h, FSR_ERR_UNSUPPORTED, "tensor-core transform variants are built for B = 4 only");
     return FSR_OK;
 }
 
@@ -129,8 +132,11 @@ int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int hei
     a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
     a.nblocks = (long long)a.im.nbx * ((height + p->block - 1) / p->block);
     a.mth = method_args(p);
-    cudaError_t e = (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_single_fp64(a, p->block, h->sm_count, stream)
-                                                      : fsrk::launch_single_fp32(a, p->block, h->sm_count, stream);
+    cudaError_t e;
+    if (p->precision == FSR_FP64_DEBUG) e = fsrk::launch_single_fp64(a, p->block, h->sm_count, stream);
+    else if (p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32)
+        e = fsrk::launch_single_fp32_tc(a, p->block, p->precision == FSR_TC_BF16X3, h->sm_count, stream);
+    else e = fsrk::launch_single_fp32(a, p->block, h->sm_count, stream);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return ok(h);
 }
@@ -149,6 +155,8 @@ int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params*
     if (!d) return fail(h, FSR_ERR_INVALID_ARG, "descs is NULL");
     int r = check_method(h, p);
     if (r != FSR_OK) return r;
+    if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
+        return fail(h, FSR_ERR_UNSUPPORTED, "the batch form runs FSR_FP32 or FSR_FP64_DEBUG");
     for (int i = 0; i < n; ++i) {
         r = check_image(h, d[i].img, d[i].mask, d[i].out, d[i].height, d[i].width, d[i].pitch, d[i].iters, true, i);
         if (r != FSR_OK) return r;
@@ -314,7 +322,7 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
                     cfg->device, prop.major, prop.minor);
     if ((e = fsrk::configure_fp32()) != cudaSuccess || (e = fsrk::configure_fp32_batch()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
-        (e = fsrk::configure_fp64_batch()) != cudaSuccess)
+        (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));
     fsr_handle* h = new (std::nothrow) fsr_handle();
     if (!h) return fail(nullptr, FSR_ERR_OOM, "host allocation of the handle failed");

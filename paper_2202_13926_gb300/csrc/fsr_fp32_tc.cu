@@ -1,0 +1,43 @@
+// FP32 iteration with the forward transform on tensor cores (precision
+// study): TF32 or BF16 hi/lo split products, FP32 accumulation; B = 4, 11
+// warps per CTA (the DFT matrix table takes the twelfth warp's shared memory).
+#include "fsr_launch.h"
+
+namespace fsrk {
+namespace {
+
+constexpr int kWarpsTc = 11;
+
+template <Dft D>
+size_t tc_smem() { return SmemLayout<float>::bytes(kWarpsTc) + TcTable<D>::bytes; }
+
+template <Dft D>
+cudaError_t configure_one() {
+    return cudaFuncSetAttribute(fsr_blocks_kernel<float, 4, kWarpsTc, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem<D>());
+}
+
+template <Dft D>
+cudaError_t launch_one(const KernelArgs& a, int sm_count, cudaStream_t stream) {
+    const size_t smem = tc_smem<D>();
+    int grid = 0;
+    cudaError_t e = persistent_grid(fsr_blocks_kernel<float, 4, kWarpsTc, D>, kWarpsTc, smem, a.nblocks, sm_count, &grid);
+    if (e != cudaSuccess) return e;
+    fsr_blocks_kernel<float, 4, kWarpsTc, D><<<grid, kWarpsTc * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t configure_fp32_tc() {
+    cudaError_t e = configure_one<Dft::TF32>();
+    if (e != cudaSuccess) return e;
+    return configure_one<Dft::BF16X3>();
+}
+
+cudaError_t launch_single_fp32_tc(const KernelArgs& a, int B, int bf16x3, int sm_count, cudaStream_t stream) {
+    if (B != 4) return cudaErrorNotSupported;
+    return bf16x3 ? launch_one<Dft::BF16X3>(a, sm_count, stream) : launch_one<Dft::TF32>(a, sm_count, stream);
+}
+
+}  // namespace fsrk

@@ -23,10 +23,13 @@ cudaError_t configure_fp32_batch();
 cudaError_t configure_fp32_sched();
 cudaError_t configure_fp64();
 cudaError_t configure_fp64_batch();
+cudaError_t configure_fp32_tc();
 
 // Single image, static schedule, 12 (FP32) or 4 (FP64) warps per CTA.
 cudaError_t launch_single_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
 cudaError_t launch_single_fp64(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
+// Forward transform on tensor cores (TF32, or BF16 hi/lo with bf16x3 = 1); B = 4 only.
+cudaError_t launch_single_fp32_tc(const KernelArgs& a, int B, int bf16x3, int sm_count, cudaStream_t stream);
 
 // Batch form.  Returns cudaErrorNotSupported for a schedule that is not
 // instantiated (see batch_schedule_supported).

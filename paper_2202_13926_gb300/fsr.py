@@ -25,7 +25,10 @@ FSR_ERR_UNSUPPORTED = 5
 
 FSR_FP32 = 0
 FSR_FP64_DEBUG = 1
-PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG}
+FSR_TC_BF16X3 = 2
+FSR_TC_TF32 = 3
+PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG, "tc_bf16x3": FSR_TC_BF16X3,
+              "tc_tf32": FSR_TC_TF32}
 
 # every function declared in include/fsr.h
 EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",

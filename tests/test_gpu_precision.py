@@ -1,0 +1,90 @@
+"""Precision study: the forward transform on tensor cores (BF16 hi/lo split
+products, TF32) against the FP32 SIMT transform and the FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import parity as PA
+from paper_2202_13926_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MODES = ("fp32", "tc_bf16x3", "tc_tf32")
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_13926_gb300 import fsr
+    h = fsr.Handle(0)
+    yield h
+    h.close()
+
+
+def _run(h, img, mask, **kw):
+    dev = torch.device("cuda:0")
+    out = h.reconstruct(torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev), **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_transform_selects_dc_then_the_cosine_pair(handle, mode):
+    """All pixels known, rho = 1, gamma = 1, no frequency weighting: W is
+    1024 delta, so every interior support of 128 + A cos(2 pi (3 y + 5 x)/32)
+    selects DC (index 0) and then the conjugate pair (3,5), (29,27) (indices
+    101 and 955, lower first).  A wrong operand layout in the tensor-core
+    transform would select something else."""
+    from paper_2202_13926_gb300 import fsr
+    H = W = 96
+    yy, xx = np.mgrid[0:H, 0:W]
+    f = (128 + 60.0 * np.cos(2 * np.pi * (3 * yy + 5 * xx) / 32 + 0.4)).astype(np.float32)
+    mask = np.ones((H, W), np.uint8)
+    dev = torch.device("cuda:0")
+    nb = (H // 4) * (W // 4)
+    seq = torch.full((nb * 3,), -1, dtype=torch.int16, device=dev)
+    handle.reconstruct(torch.from_numpy(f).to(dev), torch.from_numpy(mask).to(dev), iters=3, rho=1.0,
+                       gamma=1.0, freq_weight=False, precision=mode, seq_out=seq)
+    torch.cuda.synchronize()
+    s = seq.cpu().numpy().reshape(H // 4, W // 4, 3)
+    inner = s[4:20, 4:20].reshape(-1, 3)          # supports entirely inside the image
+    assert np.all(inner[:, 0] == 0), mode
+    assert np.all(inner[:, 1] == 101) and np.all(inner[:, 2] == 955), mode
+
+
+def test_precision_study_on_1080p_quarter_sampling(handle):
+    """The 1080p quarter-sampling frame in FP32-SIMT, BF16x3 and TF32 transform
+    modes; each against the FP64 oracle (whole frame)."""
+    img, mask = synth.fhd_quarter_case()
+    r = oracle.fsr_image_blocks(img, mask, K=100)
+    ref = oracle.assemble_image(r["target"], 1080, 1920, 4)
+    rows = {}
+    for mode in MODES:
+        got = _run(handle, img, mask, iters=100, precision=mode)
+        unk = mask == 0
+        rows[mode] = {
+            "psnr_db": PA.psnr(got, img),
+            "psnr_oracle_db": PA.psnr(ref, img),
+            "dpsnr_db": PA.psnr(got, img) - PA.psnr(ref, img),
+            "max_abs_vs_oracle": float(np.max(np.abs(got - ref))),
+            "rms_vs_oracle_unknown": float(np.sqrt(np.mean((got - ref)[unk] ** 2))),
+            "frac_within_0.5": PA.frac_within(got, ref),
+        }
+        assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    print("precision study:", json.dumps(rows, indent=1))
+    out = os.environ.get("FSR_PRECISION_REPORT")
+    if out:
+        with open(out, "w") as fh:
+            json.dump(rows, fh, indent=1)
+    assert rows["fp32"]["frac_within_0.5"] >= PA.FRAC_MIN
+    # the split-product transform keeps ~16 bits; TF32 ~11: both must stay usable
+    assert abs(rows["tc_bf16x3"]["dpsnr_db"]) <= 0.1
+    assert abs(rows["tc_tf32"]["dpsnr_db"]) <= 1.0
