@@ -145,7 +145,7 @@ typedef struct fsr_image_desc {
 
 /* Schedule of the persistent batch launch. */
 typedef struct fsr_schedule {
-    int warps;   /* warps per CTA = support blocks in flight per CTA (FP32: 12, or 4/6 for B = 4; FP64: 4) */
+    int warps;   /* warps per CTA = support blocks in flight per CTA (FP32: 16, or 8/12 for B = 4; FP64: 4) */
     int chunk;   /* blocks a warp takes per counter increment, 1..64 */
 } fsr_schedule;
 

@@ -382,11 +382,13 @@ __device__ __forceinline__ void tc_dft2(float (&zr)[S], float (&zi)[S], unsigned
     __syncwarp();
 }
 
-// Row stride (in complex elements) of the doubled W rows: 64 entries + pad,
-// chosen so that 32 lanes reading 32 different rows at one column hit
-// distinct banks (128-bit loads for FP32, 128-bit elements for FP64).
+// Row stride (in complex elements) of the stored W rows, chosen so that 32
+// lanes reading 32 different rows at one column hit distinct banks (128-bit
+// loads).  FP64 rows hold 64 entries (the row twice); FP32 rows hold 48
+// (the row and its first half again): every 16 consecutive entries of the
+// circular row are contiguous, which is what the FP32 loop reads.
 template <typename T> struct WRow;
-template <> struct WRow<float> { static constexpr int stride = 2 * S + 2; };   // 528 B
+template <> struct WRow<float> { static constexpr int stride = S + S / 2 + 2; };  // 48 entries + pad: 400 B
 template <> struct WRow<double> { static constexpr int stride = 2 * S + 1; };  // 1040 B
 
 template <typename T>
@@ -520,7 +522,7 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
         zr[l] = (ar + cr) * T(0.5);
         zi[l] = (ai - ci) * T(0.5);
         wrow_out[l] = w1;
-        wrow_out[l + S] = w1;
+        if (l + S < WS - 1) wrow_out[l + S] = w1;
         if (l == 0) W0 = w1.x;
         if (l2 != l) {
             const T br = zr[l2], bi = zi[l2];
@@ -530,7 +532,7 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
             zr[l2] = (br + dr) * T(0.5);
             zi[l2] = (bi - di) * T(0.5);
             wrow_out[l2] = w2;
-            wrow_out[l2 + S] = w2;
+            if (l2 + S < WS - 1) wrow_out[l2 + S] = w2;
         }
     }
     st.W0 = __shfl_sync(FULL, W0, 0);
@@ -601,24 +603,26 @@ __device__ __forceinline__ void pass_fold(float (&zr)[S], float (&zi)[S], const 
 }
 
 // Eq. (12) with the shifted row W[(k-u)][(l-v) mod 32], then the objective.
-// base points at entry (32-v) mod 32 of the doubled row k-u, so entry l of
-// the shifted row is base[l]; for odd offsets the 16-byte loads start one
-// entry earlier and each component takes the upper half of one load and the
-// lower half of the next.
+// Components 16h .. 16h+15 (h = 0, 1) read the 16 consecutive stored entries
+// starting at (32 - v + 16h) mod 32 of row k-u, which never wrap in the
+// 48-entry row.  For odd offsets the 16-byte loads start one entry earlier
+// and each component takes the upper half of one load and the lower half of
+// the next.
 template <bool ODD>
-__device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
-                                            const float2* base, float cr, float ci, float (&g)[NG]) {
+__device__ __forceinline__ void half_update(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
+                                            const float2* base, int h, float cr, float ci, float (&g)[NG]) {
     const float4* p = reinterpret_cast<const float4*>(ODD ? base - 1 : base);
     float4 prev = ODD ? p[0] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < S / 2; ++i) {
+    for (int j = 0; j < S / 4; ++j) {
+        const int i = 8 * h + j;     // pair index: components 2i, 2i+1
         float w0r, w0i, w1r, w1i;
         if (ODD) {
-            const float4 next = p[i + 1];
+            const float4 next = p[j + 1];
             w0r = prev.z; w0i = prev.w; w1r = next.x; w1i = next.y;
             prev = next;
         } else {
-            const float4 w = p[i];
+            const float4 w = p[j];
             w0r = w.x; w0i = w.y; w1r = w.z; w1i = w.w;
         }
         residual_update(zr[2 * i], zi[2 * i], w0r, w0i, cr, ci);
@@ -626,6 +630,13 @@ __device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], cons
         group_max(g, i, objective<float>(zr[2 * i], zi[2 * i], wf_at(wfr, 2 * i)),
                   objective<float>(zr[2 * i + 1], zi[2 * i + 1], wf_at(wfr, 2 * i + 1)));
     }
+}
+
+template <bool ODD>
+__device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
+                                            const float2* row, int s, float cr, float ci, float (&g)[NG]) {
+    half_update<ODD>(zr, zi, wfr, row + s, 0, cr, ci, g);
+    half_update<ODD>(zr, zi, wfr, row + ((s + S / 2) & (S - 1)), 1, cr, ci, g);
 }
 
 // Lane u writes components 4j..4j+3 of its row to rowbuf[0..3] (j uniform).
@@ -717,9 +728,9 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
             split = false;
         }
         const int s = (S - v) & (S - 1);
-        const float2* base = Wd + ((lane - u) & (S - 1)) * WS32 + s;
-        if (s & 1) pass_update<true>(zr, zi, wfr, base, cr, ci, g);
-        else pass_update<false>(zr, zi, wfr, base, cr, ci, g);
+        const float2* row = Wd + ((lane - u) & (S - 1)) * WS32;
+        if (s & 1) pass_update<true>(zr, zi, wfr, row, s, cr, ci, g);
+        else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
     }
 }
 
@@ -872,10 +883,10 @@ __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk
     }
 }
 
-// Register budget: FP32 CTAs are sized so that 12 warps share an SM, FP64
-// runs one CTA per SM.
+// Register budget: FP32 CTAs are sized so that 16 warps share an SM (at most
+// 128 registers per thread), FP64 runs one CTA per SM.
 template <typename T, int WARPS> struct MinBlocks { static constexpr int value = 1; };
-template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value = 12 / WARPS; };
+template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value = WARPS < 16 ? 16 / WARPS : 1; };
 
 template <typename T, int B, int WARPS, Dft DFT = Dft::SIMT>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)

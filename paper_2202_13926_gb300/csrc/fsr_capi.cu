@@ -538,7 +538,7 @@ int fsr_autotune_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_
     if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "autotune setup: %s", cudaGetErrorString(e));
-    const int warps_c[3] = {12, 6, 4};
+    const int warps_c[3] = {16, 12, 8};
     const int chunk_c[4] = {1, 2, 4, 8};
     fsrk::Schedule win = h->sched[p->precision][b_index(p->block)];
     float win_ms = -1.f;

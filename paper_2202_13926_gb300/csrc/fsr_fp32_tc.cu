@@ -1,12 +1,12 @@
 // FP32 iteration with the forward transform on tensor cores (precision
-// study): TF32 or BF16 hi/lo split products, FP32 accumulation; B = 4, 11
-// warps per CTA (the DFT matrix table takes the twelfth warp's shared memory).
+// study): TF32 or BF16 hi/lo split products, FP32 accumulation; B = 4, 15
+// warps per CTA (the DFT matrix table takes the sixteenth warp's shared memory).
 #include "fsr_launch.h"
 
 namespace fsrk {
 namespace {
 
-constexpr int kWarpsTc = 11;
+constexpr int kWarpsTc = 15;
 
 template <Dft D>
 size_t tc_smem() { return SmemLayout<float>::bytes(kWarpsTc) + TcTable<D>::bytes; }

@@ -39,7 +39,7 @@ struct fsr_handle {
     char err[512] = {0};
     std::string cache_path;
     // batch schedules per [precision][B]
-    fsrk::Schedule sched[2][fsri::kNumB] = {{{12, 1}, {12, 1}, {12, 1}, {12, 1}}, {{4, 1}, {4, 1}, {4, 1}, {4, 1}}};
+    fsrk::Schedule sched[2][fsri::kNumB] = {{{16, 1}, {16, 1}, {16, 1}, {16, 1}}, {{4, 1}, {4, 1}, {4, 1}, {4, 1}}};
     // device staging buffers of fsr_reconstruct_host
     float* d_img = nullptr;
     uint8_t* d_mask = nullptr;

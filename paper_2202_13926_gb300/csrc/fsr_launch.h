@@ -25,7 +25,7 @@ cudaError_t configure_fp64();
 cudaError_t configure_fp64_batch();
 cudaError_t configure_fp32_tc();
 
-// Single image, static schedule, 12 (FP32) or 4 (FP64) warps per CTA.
+// Single image, static schedule, 16 (FP32) or 4 (FP64) warps per CTA.
 cudaError_t launch_single_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
 cudaError_t launch_single_fp64(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
 // Forward transform on tensor cores (TF32, or BF16 hi/lo with bf16x3 = 1); B = 4 only.
@@ -37,8 +37,8 @@ cudaError_t launch_batch_fp32(const BatchArgs& a, int B, Schedule sc, int sm_cou
 cudaError_t launch_batch_fp32_sched(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 cudaError_t launch_batch_fp64(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 
-// Warps-per-CTA values instantiated for (precision, B): FP32 has 12 for every
-// B and also 4 and 6 for B = 4; FP64 has 4.
+// Warps-per-CTA values instantiated for (precision, B): FP32 has 16 for every
+// B and also 8 and 12 for B = 4; FP64 has 4.
 bool batch_schedule_supported(int fp64, int B, int warps);
 
 // Persistent grid: resident CTAs per SM x SMs, capped by the work available.

@@ -116,7 +116,7 @@ def test_every_schedule_gives_identical_results(fsr_mod, handle):
     ref = None
     saved = fsr.fsr_get_schedule(handle.ptr)
     try:
-        for warps in (12, 6, 4):
+        for warps in (16, 12, 8):
             for chunk in (1, 3, 8):
                 fsr.fsr_set_schedule(handle.ptr, warps, chunk)
                 for it in items:
@@ -131,7 +131,7 @@ def test_every_schedule_gives_identical_results(fsr_mod, handle):
     finally:
         fsr.fsr_set_schedule(handle.ptr, *saved)
     with pytest.raises(fsr.FsrError) as e:
-        fsr.fsr_set_schedule(handle.ptr, 6, 1, block=8)   # not instantiated for B = 8
+        fsr.fsr_set_schedule(handle.ptr, 8, 1, block=8)   # not instantiated for B = 8
     assert e.value.code == fsr.FSR_ERR_UNSUPPORTED
 
 
