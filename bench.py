@@ -336,6 +336,7 @@ def main():
     torch.cuda.synchronize(dev)
     _barrier(dist)
     t_wall = time.perf_counter() - t_wall0
+    handle.check_status(stream)   # no tile-copy wait gave up
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = _max_over_ranks(dist, sum(step_ms) / 1e3)

@@ -122,6 +122,29 @@ int fsr_reconstruct_host(fsr_handle *h, const float *img, const uint8_t *mask,
                          int height, int width, int pitch, const fsr_params *p,
                          float *out, void *stream);
 
+/* Support tiles (step a1 of every block, Sec. III-A, Eq. 13): when img and
+ * mask are 16-byte aligned and pitch is a multiple of 16, the single-image
+ * kernels bring each block's 32 x 32 support in by two TMA tile copies (the
+ * image and the mask), with pixels outside the image filled as unknown;
+ * otherwise by plain loads.  Both give identical results.  A warp waits for
+ * its copies with a bounded wait (about one second); when the wait gives up,
+ * the warp sets a bit in the handle's device status word and takes no more
+ * blocks (their output pixels are left unwritten).
+ *
+ * fsr_check_status synchronises `stream`, then reads and clears the status
+ * word: FSR_OK, or FSR_ERR_TIMEOUT with a message when a wait gave up in any
+ * single-image launch on h since the last check.  fsr_reconstruct_host does
+ * this check itself.  Errors: INVALID_ARG (h NULL), CUDA. */
+int fsr_check_status(fsr_handle *h, void *stream);
+
+/* Test hook (no counterpart in the paper): the next single-image launch on h
+ * that uses tile copies expects 16 bytes more per block than its copies
+ * deliver, so every wait runs out and the launch ends with FSR_ERR_TIMEOUT
+ * from fsr_check_status.  No GPU fault is involved: the copies complete, only
+ * the barrier's phase does not.  Launches after it are unaffected.
+ * Errors: INVALID_ARG (h NULL). */
+int fsr_inject_tile_wait_fault(fsr_handle *h);
+
 /* Number of target blocks N = ceil(height/B) * ceil(width/B) (Eq. 13);
  * 0 for invalid sizes. */
 long long fsr_num_blocks(int height, int width, int block);

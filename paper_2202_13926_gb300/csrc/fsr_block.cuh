@@ -11,11 +11,16 @@
 //     which makes both exactly Hermitian.  R_w = mu W + Q exactly; while only
 //     the DC basis image is selected, R_w is kept as a W + Q with the scalar
 //     a absorbing every DC update (no rounding of the spectrum); at the first
-//     other selection a W is folded into Q (see the design doc for the numerics);
-//   * W is kept in shared memory with every row stored twice in a row
-//     (W[i][0..31] W[i][0..31]), so the circularly shifted row
-//     W[(k-u) mod S][(l-v) mod S], l = 0..31 of Eqs. (12), (14), (15) is 32
-//     consecutive entries starting at column (S - v) mod S: no index wrap;
+//     other selection a W is folded into Q (this keeps the FP32 spectrum
+//     within a few ulps of the FP64 one while the DC term dominates);
+//   * W is kept in shared memory; an FP32 row holds W[i][0..31] followed by
+//     W[i][0..15] (48 entries), so the circularly shifted row
+//     W[(k-u) mod S][(l-v) mod S], l = 0..31 of Eqs. (12), (14), (15) is read
+//     as two runs of 16 consecutive entries starting at columns s and
+//     (s + 16) mod S, s = (S - v) mod S: no index wrap inside a run;
+//   * the support tile of image and mask comes in by two TMA tile copies per
+//     block (image pitch permitting); pixels outside the image arrive as the
+//     copy's zero fill, i.e. as unknown;
 //   * argmax (Eq. 8): each lane keeps the running maximum of its row, one
 //     warp max-reduction gives the maximum M, the lowest lane whose row holds
 //     M is u, that lane publishes its row, and the lowest column with
@@ -29,6 +34,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>          // CUtensorMap (type only)
 #include <cuda_runtime.h>
 
 namespace fsrk {
@@ -55,11 +61,32 @@ struct MethodArgs {
     int freq_weight;
 };
 
+// TMA descriptors of one image: the support tile of every block is one 2-D
+// tile copy of the image (kTileImgCols x 32 floats) and one of the mask
+// (kTileMaskCols x 32 bytes); coordinates are rounded down to 16-byte
+// boundaries and the lane offset is taken in shared memory.
+constexpr int kTileImgCols = S + 4;     // 144 B rows: x rounded down to a multiple of 4 floats
+constexpr int kTileMaskCols = S + 16;   // 48 B rows: x rounded down to a multiple of 16 bytes
+constexpr unsigned kTileImgBytes = 4u * kTileImgCols * S;   // 4608
+constexpr unsigned kTileMaskBytes = 1u * kTileMaskCols * S; // 1536
+constexpr unsigned kTileBytes = kTileImgBytes + kTileMaskBytes;
+struct TileMaps {
+    CUtensorMap img;    // FLOAT32 [H][W], row stride pitch * 4 B, box {kTileImgCols, S}
+    CUtensorMap mask;   // UINT8   [H][W], row stride pitch B,     box {kTileMaskCols, S}
+};
+
+// Device status word bits (set by kernels, read and cleared by the host).
+constexpr unsigned kStatusTileWait = 1u;   // a bounded wait on a tile copy gave up
+
 // Single image, static schedule.
 struct KernelArgs {
     ImageArgs im;
     long long nblocks;   // N
     MethodArgs mth;
+    unsigned* status;    // device status word (kStatus* bits)
+    int tiles;           // 1: support tiles by TMA through `maps`; 0: plain loads
+    int tx_extra;        // test hook: extra bytes each tile wait expects (0 in use)
+    TileMaps maps;
 };
 
 // Many images, dynamic schedule: warps take chunks of the concatenated block
@@ -400,10 +427,18 @@ struct SmemLayout {
     static constexpr size_t wf_off = w0_off + sizeof(T) * S * S;        // S*S T
     static constexpr size_t cs_off = wf_off + sizeof(T) * S * S;        // S T2
     static constexpr size_t warp0_off = cs_off + sizeof(T2) * S;
-    // per warp: doubled W rows, then the published row
+    // per warp: W rows, then the published row
     static constexpr size_t w_elems = (size_t)S * WS;
     static constexpr size_t per_warp = sizeof(T2) * (w_elems + S);
-    static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
+    // after the warps' areas: one tile-copy mbarrier (8 B) per warp, then the
+    // parity (4 B) of the phase each warp waits for next
+    static constexpr size_t bar_off(int warps) { return warp0_off + per_warp * (size_t)warps; }
+    static constexpr size_t parity_off(int warps) { return bar_off(warps) + 8 * (size_t)warps; }
+    static constexpr size_t bytes(int warps) { return bar_off(warps) + ((12 * (size_t)warps + 127) & ~(size_t)127); }
+    // the support tile lands in the warp's W area before that area is used;
+    // 128-byte offsets keep both tile copies' destinations aligned
+    static_assert(kTileBytes <= sizeof(T2) * w_elems, "support tile must fit the W area");
+    static_assert(warp0_off % 128 == 0 && per_warp % 128 == 0, "warp areas must be 128-byte aligned");
 };
 
 // Number of target pixels each lane accumulates for a B x B target.
@@ -416,19 +451,90 @@ struct BlockState {
     T mu;   // weighted mean of the known values: R_w = mu W + Q at the start
 };
 
-// a1-a3: load the support (lane n = column n), weight it, transform it.
-// On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
-// row k in zr/zi and every row of W is in Wd twice in a row.
-template <typename T, int WS, Dft DFT>
-__device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
-                                              const T* __restrict__ sw0,
-                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
-                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
-    using T2 = typename Vec2<T>::type;
+// ---- a1 by TMA: one tile copy of image and mask per block ----------------
+// The wait on a copy is bounded: after kTileWaitPolls polls of at most
+// kTileWaitHintNs each (about a second) the warp records kStatusTileWait in
+// the status word and stops taking blocks; the host reports FSR_ERR_TIMEOUT.
+constexpr int kTileWaitPolls = 1 << 16;
+constexpr unsigned kTileWaitHintNs = 20000;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tile_bar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Lane 0: expect `bytes` on `bar` and start both copies of the support whose
+// top-left pixel is (y0, x0).
+__device__ __forceinline__ void tile_issue(const TileMaps* maps, uint32_t dst, uint32_t bar, int y0, int x0,
+                                           unsigned bytes) {
+    const uint64_t mi = reinterpret_cast<uint64_t>(&maps->img);
+    const uint64_t mm = reinterpret_cast<uint64_t>(&maps->mask);
+    // the W area was last written and read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(mi), "r"(x0 & ~3), "r"(y0), "r"(bar)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst + kTileImgBytes), "l"(mm), "r"(x0 & ~15), "r"(y0), "r"(bar)
+        : "memory");
+}
+
+// Every lane: wait (bounded) for the phase with this parity; warp-uniform result.
+__device__ __forceinline__ bool tile_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kTileWaitPolls; ++it) {
+        if (!done)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity), "r"(kTileWaitHintNs)
+                : "memory");
+        if (__all_sync(FULL, done != 0)) return true;
+    }
+    return false;
+}
+
+// Tile copies of one block: descriptors (kernel parameters), the warp's
+// mbarrier and the shared word with the parity of its next phase.
+struct TileReq {
+    const TileMaps* maps;   // nullptr: plain loads
+    unsigned* status;
+    unsigned bytes;         // bytes expected per block
+    uint32_t bar;
+    uint32_t* parity;
+};
+
+// a1 (plain loads, or from the tile in shared memory): raw values of column
+// `lane` of the support, 0 where unknown; returns the known bits (bit m:
+// pixel (m, lane)).  Pixels outside the image are unknown.
+template <typename T>
+__device__ __forceinline__ unsigned load_support(const ImageArgs& a, int y0, int x0, int lane,
+                                                 const unsigned char* tile, T (&zr)[S]) {
+    unsigned known = 0;
+    if (tile != nullptr) {
+        const float* ti = reinterpret_cast<const float*>(tile) + (x0 & 3) + lane;
+        const unsigned char* tm = tile + kTileImgBytes + (x0 & 15) + lane;
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+            const bool kn = tm[m * kTileMaskCols] != 0;
+            const float fv = ti[m * kTileImgCols];
+            zr[m] = kn ? T(fv) : T(0);   // select: unknown values never enter arithmetic
+            known |= kn ? (1u << m) : 0u;
+        }
+        __syncwarp();   // the tile is consumed before the W area is reused
+        return known;
+    }
     const int xc = x0 + lane;
     const bool xin = (unsigned)xc < (unsigned)a.W;
-    unsigned known = 0;   // bit m: pixel (m, lane) is known
-    T sw = T(0), sfw = T(0);
 #pragma unroll
     for (int m = 0; m < S; ++m) {
         const int y = y0 + m;
@@ -439,9 +545,27 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
             kn = __ldg(a.mask + off) != 0;
             fv = __ldg(a.img + off);
         }
-        zr[m] = kn ? T(fv) : T(0);   // select: unknown values never enter arithmetic
+        zr[m] = kn ? T(fv) : T(0);
         known |= kn ? (1u << m) : 0u;
-        const T w = kn ? sw0[m * S + lane] : T(0);
+    }
+    return known;
+}
+
+// a1-a3: load the support (lane n = column n), weight it, transform it.
+// On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
+// row k in zr/zi and the W rows are in Wd (layout of WRow<T>).
+template <typename T, int WS, Dft DFT>
+__device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
+                                              const T* __restrict__ sw0,
+                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
+                                              const unsigned char* tile,
+                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
+    using T2 = typename Vec2<T>::type;
+    const unsigned known = load_support<T>(a, y0, x0, lane, tile, zr);
+    T sw = T(0), sfw = T(0);
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        const T w = ((known >> m) & 1u) ? sw0[m * S + lane] : T(0);
         sw += w;
         sfw += w * zr[m];
     }
@@ -844,15 +968,31 @@ __device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf
 }
 
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
+// With a tile context the support comes in by TMA; returns false when the
+// bounded wait for it gave up (the warp then stops taking blocks).
 template <typename T, int B, Dft DFT = Dft::SIMT>
-__device__ __forceinline__ void process_block(const ImageArgs& im, long long blk, int L, T gamma,
+__device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
-                                              const unsigned char* tctab, int lane) {
+                                              const unsigned char* tctab, const TileReq& tr, int lane) {
     constexpr int P = TargetPix<B>::P;
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
     const int y0 = by * B - L, x0 = bx * B - L;
+
+    const unsigned char* tile = nullptr;
+    if (tr.maps != nullptr) {
+        __syncwarp();   // every lane is done with the W area of the previous block
+        if (lane == 0) tile_issue(tr.maps, smem_addr(Wd), tr.bar, y0, x0, tr.bytes);
+        const uint32_t parity = *tr.parity;
+        if (!tile_wait(tr.bar, parity)) {
+            if (lane == 0) atomicOr(tr.status, kStatusTileWait);
+            return false;
+        }
+        __syncwarp();
+        if (lane == 0) *tr.parity = parity ^ 1u;
+        tile = reinterpret_cast<const unsigned char*>(Wd);
+    }
 
     T zr[S], zi[S];
     BlockState<T> st;
@@ -861,7 +1001,7 @@ __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk
     for (int q = 0; q < P; ++q) gacc[q] = T(0);
 
     int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
-    if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, zr, zi, st)) {
+    if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
         iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
         __syncwarp();   // W area free for the next block
     } else if (seq != nullptr && lane == 0) {
@@ -881,6 +1021,7 @@ __device__ __forceinline__ void process_block(const ImageArgs& im, long long blk
             }
         }
     }
+    return true;
 }
 
 // Register budget: FP32 CTAs are sized so that 16 warps share an SM (at most
@@ -890,10 +1031,10 @@ template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value
 
 template <typename T, int B, int WARPS, Dft DFT = Dft::SIMT>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
-fsr_blocks_kernel(const KernelArgs a) {
+fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
     using T2 = typename Vec2<T>::type;
     using Lay = SmemLayout<T>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
     T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
     T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
@@ -907,10 +1048,29 @@ fsr_blocks_kernel(const KernelArgs a) {
     if constexpr (DFT != Dft::SIMT) tc_table<DFT>(tctab);
     __syncthreads();
 
+    // tile copies need 128-byte aligned destinations (kept by the layout)
+    const bool tiles = a.tiles && (smem_addr(smem) & 127u) == 0;
+    if (tiles) {
+        if (lane == 0) {
+            tile_bar_init(smem_addr(smem + Lay::bar_off(WARPS) + 8 * warp));
+            reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS))[warp] = 0;
+        }
+        __syncwarp();
+    }
+
     const T gamma = T(a.mth.gamma);
     for (long long blk = (long long)blockIdx.x * WARPS + warp; blk < a.nblocks;
-         blk += (long long)gridDim.x * WARPS)
-        process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, lane);
+         blk += (long long)gridDim.x * WARPS) {
+        const int wq = threadIdx.x >> 5;
+        TileReq tr;
+        tr.maps = tiles ? &a.maps : nullptr;
+        tr.status = a.status;
+        tr.bytes = kTileBytes + (unsigned)a.tx_extra;
+        tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * wq);
+        tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + wq;
+        if (!process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, tr, lane))
+            break;
+    }
 }
 
 // Batch form: every warp takes `chunk` consecutive entries of the block list
@@ -920,7 +1080,7 @@ __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
 fsr_batch_kernel(const BatchArgs a) {
     using T2 = typename Vec2<T>::type;
     using Lay = SmemLayout<T>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
     T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
     T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
@@ -949,7 +1109,7 @@ fsr_batch_kernel(const BatchArgs a) {
             }
             const ImageArgs im = a.images[lo];
             process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
-                                rowbuf, nullptr, lane);
+                                rowbuf, nullptr, TileReq{nullptr, nullptr, 0u, 0u, nullptr}, lane);
         }
     }
 }

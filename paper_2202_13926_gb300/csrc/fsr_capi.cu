@@ -1,9 +1,11 @@
 // C-ABI of the GB300 FSR library: handles, argument checks, the batch form
 // (work tables, CUDA-graph plans, schedule autotuner) and dispatch to the
 // kernels.  Declarations and contracts: include/fsr.h.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -126,12 +128,88 @@ fsrk::ImageArgs image_args(const float* img, const uint8_t* mask, float* out, in
     return im;
 }
 
+// ---- TMA descriptors of the support tiles (a1) ------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library).
+EncodeTiled encode_tiled() {
+    static const EncodeTiled fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiled>(f);
+    }();
+    return fn;
+}
+
+// Tile copies need 16-byte aligned bases and row strides: img and mask
+// 16-byte aligned and the pitch a multiple of 16 elements (16 B of mask).
+bool tiles_possible(const float* img, const uint8_t* mask, int pitch) {
+    return (reinterpret_cast<uintptr_t>(img) & 15) == 0 && (reinterpret_cast<uintptr_t>(mask) & 15) == 0 &&
+           pitch % 16 == 0;
+}
+
+// Encodes the image and mask descriptors: [H][W] with row stride pitch,
+// boxes of kTileImgCols x S floats and kTileMaskCols x S bytes, zero fill
+// outside the image (a pixel outside is unknown).
+int encode_tile_maps(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                     fsrk::TileMaps* maps) {
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return fail(h, FSR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint64_t istr[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint32_t ibox[2] = {(cuuint32_t)fsrk::kTileImgCols, (cuuint32_t)fsrk::S};
+    CUresult r = enc(&maps->img, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), dims, istr, ibox, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, FSR_ERR_CUDA, "cuTensorMapEncodeTiled (image): error %d", (int)r);
+    const cuuint64_t mstr[1] = {(cuuint64_t)pitch};
+    const cuuint32_t mbox[2] = {(cuuint32_t)fsrk::kTileMaskCols, (cuuint32_t)fsrk::S};
+    r = enc(&maps->mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(mask), dims, mstr, mbox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, FSR_ERR_CUDA, "cuTensorMapEncodeTiled (mask): error %d", (int)r);
+    return FSR_OK;
+}
+
+// Reads and clears the status word (the device must be idle for the handle's
+// single-image work); FSR_ERR_TIMEOUT when a kernel's bounded wait gave up.
+int read_status(fsr_handle* h) {
+    unsigned st = 0;
+    cudaError_t e = cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "reading the status word: %s", cudaGetErrorString(e));
+    if (st == 0) return ok(h);
+    if ((e = cudaMemset(h->d_status, 0, sizeof st)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "clearing the status word: %s", cudaGetErrorString(e));
+    return fail(h, FSR_ERR_TIMEOUT,
+                "status 0x%x: a kernel's bounded wait for a support-tile copy gave up; the warps concerned "
+                "stopped and their remaining blocks were not written",
+                st);
+}
+
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                    const fsr_params* p, float* out, cudaStream_t stream) {
     fsrk::KernelArgs a;
+    std::memset(&a, 0, sizeof a);
     a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
     a.nblocks = (long long)a.im.nbx * ((height + p->block - 1) / p->block);
     a.mth = method_args(p);
+    a.status = h->d_status;
+    if (tiles_possible(img, mask, pitch)) {
+        const int r = encode_tile_maps(h, img, mask, height, width, pitch, &a.maps);
+        if (r != FSR_OK) return r;
+        a.tiles = 1;
+        a.tx_extra = h->inject_tile_fault ? 16 : 0;
+        h->inject_tile_fault = 0;
+    }
     cudaError_t e;
     if (p->precision == FSR_FP64_DEBUG) e = fsrk::launch_single_fp64(a, p->block, h->sm_count, stream);
     else if (p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32)
@@ -330,6 +408,14 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
         delete h;
         return fail(nullptr, FSR_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
     }
+    if ((e = cudaMalloc(&h->d_status, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(h->d_status, 0, sizeof(unsigned))) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->d_status);
+        cudaEventDestroy(h->table_free);
+        delete h;
+        return fail(nullptr, FSR_ERR_OOM, "device status word: %s", cudaGetErrorString(e));
+    }
     h->device = cfg->device;
     h->sm_count = prop.multiProcessorCount;
     snprintf(h->device_name, sizeof h->device_name, "%s", prop.name);
@@ -350,6 +436,7 @@ int fsr_destroy(fsr_handle* h) {
             cudaFree(h->d_mask);
             cudaFree(h->d_out);
             cudaFree(h->d_table);
+            cudaFree(h->d_status);
             if (h->h_table) cudaFreeHost(h->h_table);
             if (h->table_free) cudaEventDestroy(h->table_free);
         }
@@ -429,6 +516,22 @@ int fsr_reconstruct_host(fsr_handle* h, const float* img, const uint8_t* mask, i
         return fail(h, FSR_ERR_CUDA, "device-to-host copy: %s", cudaGetErrorString(e));
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return read_status(h);
+}
+
+int fsr_check_status(fsr_handle* h, void* stream) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard g;
+    cudaError_t e = g.set(h->device);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return read_status(h);
+}
+
+int fsr_inject_tile_wait_fault(fsr_handle* h) {
+    if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
+    h->inject_tile_fault = 1;
     return ok(h);
 }
 
@@ -455,6 +558,7 @@ int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const f
         if (cudaMalloc(&h->d_table, bytes) != cudaSuccess || cudaMallocHost(&h->h_table, bytes) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(h->d_table);
+            cudaFree(h->d_status);
             if (h->h_table) cudaFreeHost(h->h_table);
             h->d_table = nullptr;
             h->h_table = nullptr;

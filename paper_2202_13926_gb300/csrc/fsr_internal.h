@@ -50,4 +50,7 @@ struct fsr_handle {
     void* h_table = nullptr;       // pinned host staging of the table
     size_t table_bytes = 0;
     cudaEvent_t table_free = nullptr;
+    // device status word of the single-image kernels (fsrk::kStatus* bits)
+    unsigned* d_status = nullptr;
+    int inject_tile_fault = 0;     // test hook: next tile-copy launch waits for bytes that never come
 };

@@ -36,7 +36,8 @@ EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
             "fsr_batch_create", "fsr_batch_launch", "fsr_batch_destroy",
             "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule",
             "fsr_reconstruct_batch_static", "fsr_server_create", "fsr_server_submit",
-            "fsr_server_poll", "fsr_server_stats", "fsr_server_destroy")
+            "fsr_server_poll", "fsr_server_stats", "fsr_server_destroy",
+            "fsr_check_status", "fsr_inject_tile_wait_fault")
 
 
 class FsrError(RuntimeError):
@@ -123,12 +124,14 @@ def load_library(path: str | None = None):
         lib.fsr_server_stats.argtypes = [vp, llp, llp, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), llp, ctypes.POINTER(ctypes.c_size_t)]
         lib.fsr_server_destroy.argtypes = [vp]
+        lib.fsr_check_status.argtypes = [vp, vp]
+        lib.fsr_inject_tile_wait_fault.argtypes = [vp]
         for name in ("fsr_server_create", "fsr_server_submit", "fsr_server_poll",
                      "fsr_server_stats", "fsr_server_destroy"):
             getattr(lib, name).restype = ip
         for name in ("fsr_reconstruct_batch_static", "fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
                      "fsr_batch_destroy", "fsr_autotune_batch", "fsr_get_schedule",
-                     "fsr_set_schedule"):
+                     "fsr_set_schedule", "fsr_check_status", "fsr_inject_tile_wait_fault"):
             getattr(lib, name).restype = ip
         if path is None:
             _lib = lib
@@ -225,6 +228,27 @@ def fsr_reconstruct_host(handle, img, mask, params: fsr_params, out, stream=None
         stream = stream.cuda_stream
     _check(load_library().fsr_reconstruct_host(handle, img.data_ptr(), mask.data_ptr(), H, W, pitch,
                                                ctypes.byref(params), out.data_ptr(), stream), handle)
+
+
+def _stream_ptr(stream, device=None):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return stream
+
+
+def fsr_check_status(handle, stream=None) -> None:
+    """Synchronise ``stream`` and raise FsrError(FSR_ERR_TIMEOUT) when a
+    bounded tile-copy wait of a single-image launch gave up."""
+    _check(load_library().fsr_check_status(handle, _stream_ptr(stream)), handle)
+
+
+def fsr_inject_tile_wait_fault(handle) -> None:
+    """Test hook: the next tile-copy launch on ``handle`` waits for bytes
+    that never arrive, so its bounded waits run out (no GPU fault)."""
+    _check(load_library().fsr_inject_tile_wait_fault(handle), handle)
 
 
 def image_desc(img, mask, out, iters: int, seq_out=None) -> fsr_image_desc:
@@ -349,6 +373,9 @@ class Handle:
             out = np.empty(img.shape, np.float32)
         fsr_reconstruct_host(self.ptr, img, mask, make_params(**kw), out, stream)
         return out
+
+    def check_status(self, stream=None):
+        fsr_check_status(self.ptr, stream)
 
 
 # ---- serving form ------------------------------------------------------------
