@@ -682,20 +682,31 @@ __device__ __forceinline__ void residual_update(T& re, T& im, T wr, T wi, T cr, 
 // ---------------------------------------------------------------- FP32 loop
 // Lane k holds Q[k][l] in zr[l], zi[l] and w_f[k][l] in wfr[min(l, 32-l)].
 // Every pass leaves in g[j] the maximum of the objective over the group of
-// four components 4j..4j+3 of the lane's row (short, independent max chains);
-// the argmax then needs only the one group that holds the block maximum.
+// GS components GS*j .. GS*j+GS-1 of the lane's row (short, independent max
+// chains); the argmax then needs only the one group that holds the block
+// maximum.
 
 constexpr int WS32 = WRow<float>::stride;
-constexpr int NG = 8;            // groups of four components per row
+constexpr int NG = 2;            // groups per row
+constexpr int GS = S / NG;       // components per group
+static_assert(GS % 4 == 0 && GS <= 16, "a group is published as GS / 4 float4 stores");
 
 __device__ __forceinline__ float wf_at(const float (&wfr)[S / 2 + 1], int l) {
     return wfr[l <= S / 2 ? l : S - l];
 }
 
 __device__ __forceinline__ void group_max(float (&g)[NG], int i, float o0, float o1) {
-    // pair i = components 2i, 2i+1 belongs to group i / 2
-    if ((i & 1) == 0) g[i >> 1] = fmaxf(o0, o1);
-    else g[i >> 1] = max3(g[i >> 1], o0, o1);
+    // pair i = components 2i, 2i+1 belongs to group i / (GS / 2)
+    constexpr int PPG = GS / 2;
+    if (i % PPG == 0) g[i / PPG] = fmaxf(o0, o1);
+    else g[i / PPG] = max3(g[i / PPG], o0, o1);
+}
+
+// maximum over the groups
+__device__ __forceinline__ float groups_max(const float (&g)[NG]) {
+    if constexpr (NG == 8) return max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]), fmaxf(g[6], g[7]));
+    else if constexpr (NG == 4) return fmaxf(max3(g[0], g[1], g[2]), g[3]);
+    else return fmaxf(g[0], g[1]);
 }
 
 // objective pass of R = a W + Q over the unshifted row k (DC phase)
@@ -763,17 +774,26 @@ __device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], cons
     half_update<ODD>(zr, zi, wfr, row + ((s + S / 2) & (S - 1)), 1, cr, ci, g);
 }
 
-// Lane u writes components 4j..4j+3 of its row to rowbuf[0..3] (j uniform).
+// Lane u writes components GS*j .. GS*j+GS-1 of its row to rowbuf[0..GS-1]
+// (j uniform).
+template <int J>
+__device__ __forceinline__ void store_group(const float (&zr)[S], const float (&zi)[S], float4* pub) {
+    if constexpr (J < NG) {
+#pragma unroll
+        for (int t = 0; t < GS / 2; ++t) {
+            const int c = GS * J + 2 * t;
+            pub[t] = make_float4(zr[c], zi[c], zr[c + 1], zi[c + 1]);
+        }
+    }
+}
+
 __device__ __forceinline__ void publish_group(const float (&zr)[S], const float (&zi)[S], int j,
                                               bool mine, float2* rowbuf) {
     float4* pub = reinterpret_cast<float4*>(rowbuf);
     switch (j) {
-#define FSR_PUB_CASE(J)                                                                      \
-        case J:                                                                              \
-            if (mine) {                                                                      \
-                pub[0] = make_float4(zr[4 * J], zi[4 * J], zr[4 * J + 1], zi[4 * J + 1]);     \
-                pub[1] = make_float4(zr[4 * J + 2], zi[4 * J + 2], zr[4 * J + 3], zi[4 * J + 3]); \
-            }                                                                                \
+#define FSR_PUB_CASE(J)                               \
+        case J:                                       \
+            if (mine) store_group<J>(zr, zi, pub);    \
             break;
         FSR_PUB_CASE(0) FSR_PUB_CASE(1) FSR_PUB_CASE(2) FSR_PUB_CASE(3)
         FSR_PUB_CASE(4) FSR_PUB_CASE(5) FSR_PUB_CASE(6) FSR_PUB_CASE(7)
@@ -782,12 +802,74 @@ __device__ __forceinline__ void publish_group(const float (&zr)[S], const float 
     }
 }
 
+// a5: argmax with the lowest linear index on ties.  Returns (u, v) and R[u][v];
+// SPLIT: the spectrum is R = a W + Q (DC phase).
+struct Pick {
+    int u, v;
+    float Rr, Ri;
+};
+
+template <bool SPLIT>
+__device__ __forceinline__ Pick argmax_pick(const float (&zr)[S], const float (&zi)[S], const float (&g)[NG],
+                                            const float2* Wd, float2* rowbuf, const float* __restrict__ swf,
+                                            float ar, float ai, int lane) {
+    const float m = groups_max(g);
+    const unsigned Mb = __reduce_max_sync(FULL, __float_as_uint(m));
+    const int u = __ffs(__ballot_sync(FULL, __float_as_uint(m) == Mb)) - 1;
+    // first group of this lane's row that holds the maximum (used from lane u)
+    int jg = NG - 1;
+#pragma unroll
+    for (int j = NG - 2; j >= 0; --j) jg = (__float_as_uint(g[j]) == Mb) ? j : jg;
+    jg = __shfl_sync(FULL, jg, u);
+    publish_group(zr, zi, jg, lane == u, rowbuf);
+    __syncwarp();
+    const int cl = GS * jg + (lane & (GS - 1));   // column examined by this lane
+    const float2 q = rowbuf[lane & (GS - 1)];
+    float rr = q.x, ri = q.y;
+    if constexpr (SPLIT) {
+        const float2 w = Wd[u * WS32 + cl];
+        split_value(ar, ai, w.x, w.y, q.x, q.y, rr, ri);
+    }
+    const float o = objective<float>(rr, ri, swf[u * S + cl]);
+    const int vl = __ffs(__ballot_sync(FULL, __float_as_uint(o) == Mb)) - 1;   // lanes 0..GS-1 lead
+    Pick pk;
+    pk.u = u;
+    pk.v = GS * jg + vl;
+    pk.Rr = __shfl_sync(FULL, rr, vl);
+    pk.Ri = __shfl_sync(FULL, ri, vl);
+    __syncwarp();
+    return pk;
+}
+
+// a6 for the pick of iteration nu: c = gamma p, p = R[u,v] / W[0,0]
+// (Eqs. 10-11); records the index and adds Re(c e^{+j2pi(um+vn)/S}) to the
+// target pixels (sparse inverse of G).
+template <int B>
+__device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float invW0, int nu, int lane,
+                                            int16_t* seq, const float2* __restrict__ scs,
+                                            const int (&pm)[TargetPix<B>::P], const int (&pn)[TargetPix<B>::P],
+                                            float (&gacc)[TargetPix<B>::P], float& cr, float& ci) {
+    cr = gamma * (pk.Rr * invW0);
+    ci = gamma * (pk.Ri * invW0);
+    if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(pk.u * S + pk.v);
+#pragma unroll
+    for (int q2 = 0; q2 < TargetPix<B>::P; ++q2) {
+        const float2 cs = scs[(pk.u * pm[q2] + pk.v * pn[q2]) & (S - 1)];
+        gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+    }
+}
+
+// a4-a8 for one block.  Two loops: while only the DC basis image is
+// selected, R stays a W + Q (DC phase); at the first other selection a W is
+// folded into Q and the plain loop runs the remaining iterations.  The
+// residual update after the last selection is not needed and not done.
 template <int B>
 __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* Wd, float2* rowbuf,
                                         const float* __restrict__ swf, const float2* __restrict__ scs,
                                         const BlockState<float>& st, float gamma, int K, int L, int lane,
                                         int16_t* seq, float (&gacc)[TargetPix<B>::P]) {
     constexpr int P = TargetPix<B>::P;
+    if (K <= 0) return;
     float wfr[S / 2 + 1];
 #pragma unroll
     for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
@@ -799,62 +881,36 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
     }
     const float invW0 = 1.f / st.W0;
     const float2* wrow_k = Wd + lane * WS32;
-    float ar = st.mu, ai = 0.f;
-    bool split = true;   // R = a W + Q until the first non-DC selection
     float g[NG];
-    pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
+    float cr, ci;
+    Pick pk;
+    int nu = 0;
 
-    for (int nu = 0; nu < K; ++nu) {
-        // ---- a5: argmax with the lowest linear index on ties ----
-        const float m = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]), fmaxf(g[6], g[7]));
-        const unsigned Mb = __reduce_max_sync(FULL, __float_as_uint(m));
-        const int u = __ffs(__ballot_sync(FULL, __float_as_uint(m) == Mb)) - 1;
-        // first group of this lane's row that holds the maximum (used from lane u)
-        int jg = NG - 1;
-#pragma unroll
-        for (int j = NG - 2; j >= 0; --j) jg = (__float_as_uint(g[j]) == Mb) ? j : jg;
-        jg = __shfl_sync(FULL, jg, u);
-        publish_group(zr, zi, jg, lane == u, rowbuf);
-        __syncwarp();
-        const int cl = 4 * jg + (lane & 3);      // column examined by this lane
-        const float2 q = rowbuf[lane & 3];
-        float rr = q.x, ri = q.y;
-        if (split) {
-            const float2 w = Wd[u * WS32 + cl];
-            split_value(ar, ai, w.x, w.y, q.x, q.y, rr, ri);
+    // ---- DC phase: R = a W + Q ----
+    {
+        float ar = st.mu, ai = 0.f;
+        pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
+        for (;;) {
+            pk = argmax_pick<true>(zr, zi, g, Wd, rowbuf, swf, ar, ai, lane);
+            record_pick<B>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, cr, ci);
+            if (++nu == K) return;
+            if ((pk.u | pk.v) != 0) break;
+            ar -= cr;
+            ai -= ci;
+            pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
         }
-        const float o = objective<float>(rr, ri, swf[u * S + cl]);
-        const int vl = __ffs(__ballot_sync(FULL, __float_as_uint(o) == Mb)) - 1;   // lanes 0..3 lead
-        const int v = 4 * jg + vl;
-        const float Rr = __shfl_sync(FULL, rr, vl);
-        const float Ri = __shfl_sync(FULL, ri, vl);
-        __syncwarp();
+        pass_fold(zr, zi, wrow_k, ar, ai);
+    }
 
-        // ---- a6: c = gamma p, p = R[u,v] / W[0,0] (Eqs. 10-11) ----
-        const float cr = gamma * (Rr * invW0);
-        const float ci = gamma * (Ri * invW0);
-        if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * S + v);
-#pragma unroll
-        for (int q2 = 0; q2 < P; ++q2) {
-            const float2 cs = scs[(u * pm[q2] + v * pn[q2]) & (S - 1)];
-            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
-        }
-
-        // ---- a7: residual update (or DC bookkeeping), next objective ----
-        if (split) {
-            if ((u | v) == 0) {
-                ar -= cr;
-                ai -= ci;
-                pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
-                continue;
-            }
-            pass_fold(zr, zi, wrow_k, ar, ai);
-            split = false;
-        }
-        const int s = (S - v) & (S - 1);
-        const float2* row = Wd + ((lane - u) & (S - 1)) * WS32;
+    // ---- a7 (Eq. 12) for the last pick, then a4-a6 of the next iteration ----
+    for (;;) {
+        const int s = (S - pk.v) & (S - 1);
+        const float2* row = Wd + ((lane - pk.u) & (S - 1)) * WS32;
         if (s & 1) pass_update<true>(zr, zi, wfr, row, s, cr, ci, g);
         else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
+        pk = argmax_pick<false>(zr, zi, g, Wd, rowbuf, swf, 0.f, 0.f, lane);
+        record_pick<B>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, cr, ci);
+        if (++nu == K) return;
     }
 }
 
