@@ -433,7 +433,7 @@ def main():
                           "psnr_gpu_db": psnr(got), "psnr_oracle_db": psnr(ref),
                           "dpsnr_db": dpsnr, "pass": bool(frac >= 0.999 and dpsnr <= 0.01),
                           "blocks_checked": int(len(ids))}
-        # precision study: forward transform on tensor cores, same sample
+        # precision study: forward and inverse transforms on tensor cores, same sample
         study = {}
         for mode in ("fp32", "tc_bf16x3", "tc_tf32"):
             pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, precision=mode)

@@ -52,7 +52,9 @@ extern "C" {
 #define FSR_FP32       0  /* FP32 everywhere (the production path) */
 #define FSR_FP64_DEBUG 1  /* FP64 everywhere; selection sequences comparable with an FP64 reference */
 /* Precision study (single-image entry points, B = 4): the forward 2-D DFT of
- * a3 on tensor cores with FP32 accumulation, the iteration in FP32. */
+ * the support and the inverse 2-D DFT of the model coefficients on tensor
+ * cores with FP32 accumulation; the iteration in FP32; W[0][0] of Eq. (10)
+ * summed in FP64 from the weights. */
 #define FSR_TC_BF16X3  2  /* operands split into BF16 hi + lo, products hi.hi + hi.lo + lo.hi */
 #define FSR_TC_TF32    3  /* operands rounded to TF32 */
 

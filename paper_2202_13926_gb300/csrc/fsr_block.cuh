@@ -563,17 +563,20 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
     using T2 = typename Vec2<T>::type;
     const unsigned known = load_support<T>(a, y0, x0, lane, tile, zr);
     T sw = T(0), sfw = T(0);
+    double swd = 0.0;   // precision study: W[0][0] = sum of w in FP64
 #pragma unroll
     for (int m = 0; m < S; ++m) {
         const T w = ((known >> m) & 1u) ? sw0[m * S + lane] : T(0);
         sw += w;
         sfw += w * zr[m];
+        if constexpr (DFT != Dft::SIMT) swd += double(w);
     }
     if (__ballot_sync(FULL, known != 0) == 0) return false;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sw += __shfl_xor_sync(FULL, sw, o);
         sfw += __shfl_xor_sync(FULL, sfw, o);
+        if constexpr (DFT != Dft::SIMT) swd += __shfl_xor_sync(FULL, swd, o);
     }
     const T mu = sfw / sw;   // any value works; the weighted mean makes Q[0][0] ~ 0
     st.mu = mu;
@@ -660,6 +663,9 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
         }
     }
     st.W0 = __shfl_sync(FULL, W0, 0);
+    // precision study: the normalisation of Eq. (10) uses W[0][0] summed in
+    // FP64 from the weights, not the reduced-precision GEMM output
+    if constexpr (DFT != Dft::SIMT) st.W0 = T(swd);
     __syncwarp();
     return true;
 }
@@ -843,19 +849,30 @@ __device__ __forceinline__ Pick argmax_pick(const float (&zr)[S], const float (&
 
 // a6 for the pick of iteration nu: c = gamma p, p = R[u,v] / W[0,0]
 // (Eqs. 10-11); records the index and adds Re(c e^{+j2pi(um+vn)/S}) to the
-// target pixels (sparse inverse of G).
-template <int B>
+// target pixels (sparse inverse of G).  DENSE (precision study): c is added
+// to the dense coefficient array gd[u][v] instead (G of Eq. 11 divided by
+// S^2), whose inverse transform runs on tensor cores after the loop.
+template <int B, bool DENSE>
 __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float invW0, int nu, int lane,
                                             int16_t* seq, const float2* __restrict__ scs,
                                             const int (&pm)[TargetPix<B>::P], const int (&pn)[TargetPix<B>::P],
-                                            float (&gacc)[TargetPix<B>::P], float& cr, float& ci) {
+                                            float (&gacc)[TargetPix<B>::P], float2* gd, float& cr, float& ci) {
     cr = gamma * (pk.Rr * invW0);
     ci = gamma * (pk.Ri * invW0);
     if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(pk.u * S + pk.v);
+    if constexpr (DENSE) {
+        if (lane == 0) {
+            float2 gv = gd[pk.u * S + pk.v];
+            gv.x += cr;
+            gv.y += ci;
+            gd[pk.u * S + pk.v] = gv;
+        }
+    } else {
 #pragma unroll
-    for (int q2 = 0; q2 < TargetPix<B>::P; ++q2) {
-        const float2 cs = scs[(pk.u * pm[q2] + pk.v * pn[q2]) & (S - 1)];
-        gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+        for (int q2 = 0; q2 < TargetPix<B>::P; ++q2) {
+            const float2 cs = scs[(pk.u * pm[q2] + pk.v * pn[q2]) & (S - 1)];
+            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+        }
     }
 }
 
@@ -863,11 +880,11 @@ __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float i
 // selected, R stays a W + Q (DC phase); at the first other selection a W is
 // folded into Q and the plain loop runs the remaining iterations.  The
 // residual update after the last selection is not needed and not done.
-template <int B>
+template <int B, bool DENSE = false>
 __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* Wd, float2* rowbuf,
                                         const float* __restrict__ swf, const float2* __restrict__ scs,
                                         const BlockState<float>& st, float gamma, int K, int L, int lane,
-                                        int16_t* seq, float (&gacc)[TargetPix<B>::P]) {
+                                        int16_t* seq, float (&gacc)[TargetPix<B>::P], float2* gd = nullptr) {
     constexpr int P = TargetPix<B>::P;
     if (K <= 0) return;
     float wfr[S / 2 + 1];
@@ -892,7 +909,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
         pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
         for (;;) {
             pk = argmax_pick<true>(zr, zi, g, Wd, rowbuf, swf, ar, ai, lane);
-            record_pick<B>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, cr, ci);
+            record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci);
             if (++nu == K) return;
             if ((pk.u | pk.v) != 0) break;
             ar -= cr;
@@ -909,7 +926,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
         if (s & 1) pass_update<true>(zr, zi, wfr, row, s, cr, ci, g);
         else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
         pk = argmax_pick<false>(zr, zi, g, Wd, rowbuf, swf, 0.f, 0.f, lane);
-        record_pick<B>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, cr, ci);
+        record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci);
         if (++nu == K) return;
     }
 }
@@ -1023,6 +1040,39 @@ __device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf
     }
 }
 
+// a9 on tensor cores (precision study): Re g = Re IDFT2(G) = Re DFT2(conj Gc)
+// with Gc = G / S^2 the summed coefficients c, evaluated densely by the same
+// two GEMM passes as the forward transform; the B x B target values are
+// gathered through shared memory into gacc (target pixel t of the block is
+// (L + t / B, L + t % B), L = (S - B) / 2).
+template <int B, Dft DFT, typename T>
+__device__ __forceinline__ void dense_inverse_targets(const float2* gd, typename Vec2<T>::type* Wd,
+                                                      typename Vec2<T>::type* rowbuf, const unsigned char* tctab,
+                                                      int lane, T (&zr)[S], T (&zi)[S],
+                                                      T (&gacc)[TargetPix<B>::P]) {
+    constexpr int LB = (S - B) / 2;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < S; ++m) {   // lane n: column n of conj(Gc)
+        const float2 gv = gd[m * S + lane];
+        zr[m] = gv.x;
+        zi[m] = -gv.y;
+    }
+    tc_dft2<DFT>(zr, zi, reinterpret_cast<unsigned char*>(Wd), tctab, lane);   // lane k: row k
+    float* tb = reinterpret_cast<float*>(rowbuf);
+    if (lane >= LB && lane < LB + B) {
+#pragma unroll
+        for (int c = 0; c < B; ++c) tb[(lane - LB) * B + c] = zr[LB + c];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < TargetPix<B>::P; ++q) {
+        const int pidx = lane + 32 * q;
+        gacc[q] = pidx < B * B ? tb[pidx] : T(0);
+    }
+    __syncwarp();
+}
+
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
 // With a tile context the support comes in by TMA; returns false when the
 // bounded wait for it gave up (the warp then stops taking blocks).
@@ -1057,11 +1107,28 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
     for (int q = 0; q < P; ++q) gacc[q] = T(0);
 
     int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
-    if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
-        iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
-        __syncwarp();   // W area free for the next block
-    } else if (seq != nullptr && lane == 0) {
-        for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+    if constexpr (DFT != Dft::SIMT) {
+        // precision study: dense coefficients of this block (warp's own 8 KB
+        // after the DFT table), inverse transform on tensor cores (a9)
+        float2* gd = reinterpret_cast<float2*>(const_cast<unsigned char*>(tctab) + TcTable<DFT>::bytes) +
+                     (threadIdx.x >> 5) * S * S;
+        float4* grow = reinterpret_cast<float4*>(gd + lane * S);
+#pragma unroll
+        for (int c = 0; c < S / 2; ++c) grow[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
+            iterate<B, true>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc, gd);
+            dense_inverse_targets<B, DFT>(gd, Wd, rowbuf, tctab, lane, zr, zi, gacc);
+        } else if (seq != nullptr && lane == 0) {
+            for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+        }
+    } else {
+        if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
+            iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
+            __syncwarp();   // W area free for the next block
+        } else if (seq != nullptr && lane == 0) {
+            for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+        }
     }
 
     // ---- a9: write-back of the B x B target ----

@@ -1,15 +1,18 @@
-// FP32 iteration with the forward transform on tensor cores (precision
-// study): TF32 or BF16 hi/lo split products, FP32 accumulation; B = 4, 15
-// warps per CTA (the DFT matrix table takes the sixteenth warp's shared memory).
+// FP32 iteration with the forward and the inverse transform on tensor cores
+// (precision study): TF32 or BF16 hi/lo split products, FP32 accumulation;
+// B = 4, 9 warps per CTA (shared memory: the DFT matrix table and a dense
+// 8 KB coefficient array per warp besides the W rows).
 #include "fsr_launch.h"
 
 namespace fsrk {
 namespace {
 
-constexpr int kWarpsTc = 15;
+constexpr int kWarpsTc = 9;
 
 template <Dft D>
-size_t tc_smem() { return SmemLayout<float>::bytes(kWarpsTc) + TcTable<D>::bytes; }
+size_t tc_smem() {
+    return SmemLayout<float>::bytes(kWarpsTc) + TcTable<D>::bytes + sizeof(float2) * S * S * kWarpsTc;
+}
 
 template <Dft D>
 cudaError_t configure_one() {

@@ -1,5 +1,5 @@
-"""Precision study: the forward transform on tensor cores (BF16 hi/lo split
-products, TF32) against the FP32 SIMT transform and the FP64 oracle."""
+"""Precision study: the forward and the inverse 2-D DFT on tensor cores (BF16
+hi/lo split products, TF32) against the FP32 SIMT path and the FP64 oracle."""
 import json
 import os
 
@@ -58,6 +58,28 @@ def test_transform_selects_dc_then_the_cosine_pair(handle, mode):
     inner = s[4:20, 4:20].reshape(-1, 3)          # supports entirely inside the image
     assert np.all(inner[:, 0] == 0), mode
     assert np.all(inner[:, 1] == 101) and np.all(inner[:, 2] == 955), mode
+
+
+@pytest.mark.parametrize("mode,tol", [("fp32", 2e-3), ("tc_bf16x3", 2e-2), ("tc_tf32", 0.5)])
+def test_inverse_transform_recovers_the_cosine(handle, mode, tol):
+    """One unknown pixel per 4 x 4 block (rows 1 mod 4, columns 2 mod 4),
+    rho = 1, gamma = 1, no frequency weighting, K = 3, f = 128 + A cos of
+    frequency (3, 5).  In an interior support the lost grid only couples
+    frequencies 8 apart, so the picks are DC, (3,5), (29,27), each projection
+    is exact and the model equals f: the unknown pixels come back from the
+    inverse transform (on tensor cores in the TC modes, from the sparse
+    accumulation in FP32) within the mode's rounding."""
+    H = W = 96
+    yy, xx = np.mgrid[0:H, 0:W]
+    f = (128 + 60.0 * np.cos(2 * np.pi * (3 * yy + 5 * xx) / 32 + 0.4)).astype(np.float32)
+    mask = np.ones((H, W), np.uint8)
+    mask[1::4, 2::4] = 0
+    got = _run(handle, f, mask, iters=3, rho=1.0, gamma=1.0, freq_weight=False, precision=mode)
+    inner = np.zeros((H, W), bool)
+    inner[16:80, 16:80] = True                      # blocks whose supports lie inside the image
+    sel = inner & (mask == 0)
+    err = np.abs(got[sel] - f[sel].astype(np.float64))
+    assert err.max() <= tol, (mode, err.max())
 
 
 def test_precision_study_on_1080p_quarter_sampling(handle):
