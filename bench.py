@@ -31,6 +31,15 @@ IMG_SEED = 2
 METRIC = "megapixels/s and 1080p fps at K=100 within oracle tolerance; p50/p99 serving latency"
 SMEM_BYTES_PER_CLK_SM = 128          # shared-memory bandwidth per SM per clock
 FP32_LANES_PER_SM = 128              # FP32 FMA lanes per SM
+# The paper's own timing of this path (other hardware and images; context only,
+# not the same workload: 1200x1200 TECNICK images, iteration count not stated).
+PAPER_CONTEXT = {
+    "source": "Regensky et al., Fig. 3: register-based argmax, S = 32, B = 4, quarter sampling",
+    "hardware": "NVIDIA RTX 2080 Ti",
+    "seconds_per_1200x1200_image": 0.2276,
+    "mp_per_s": 1.44 / 0.2276,
+    "fhd_fps_at_S16": 8.86,
+}
 W_BYTES_PER_COMPONENT_ITER = 8       # complex FP32 W entry read per component per iteration
 FLOPS_PER_COMPONENT_ITER = 11        # objective 3 + complex multiply-subtract 8
 
@@ -65,9 +74,9 @@ def _max_over_ranks(dist, x: float) -> float:
     return float(t.item())
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the top kernel from the committed ncu summary,
-    or None when the kernel sources changed since that capture."""
+def _profile():
+    """The committed ncu summary of the top kernel, or None when the kernel
+    sources changed since that capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "fsr_blocks_kernel_fp32_1080p_K100.json")
     if not os.path.exists(p):
@@ -80,7 +89,29 @@ def _profiled_traffic():
             m.update(fh.read())
     if m.hexdigest() != prof.get("kernel_source_sha256"):
         return None
-    return prof["dram_bytes_read"] + prof["dram_bytes_write"]
+    return prof
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the top kernel (ncu), or None."""
+    prof = _profile()
+    return None if prof is None else prof["dram_bytes_read"] + prof["dram_bytes_write"]
+
+
+def _counters(smem_peak_gbs):
+    """Unit utilisation of the top kernel from the ncu counters of the same
+    capture (None when the kernel changed since)."""
+    prof = _profile()
+    if prof is None:
+        return None
+    dur = prof["duration_ms"] * 1e-3
+    smem_gbs = prof["smem_wavefronts"] * 128 / dur / 1e9
+    return {"source": "profiles/fsr_blocks_kernel_fp32_1080p_K100.json (ncu --set full, one launch)",
+            "duration_ms": dur * 1e3,
+            "smem_pipe_gbs": smem_gbs, "smem_pipe_frac": smem_gbs / smem_peak_gbs,
+            "smem_note": "all shared-memory wavefronts x 128 B (W stream, tile, transposes, publication, conflicts)",
+            "fma_pipe_frac": prof["fma_pipe_pct"] / 100, "issue_active_frac": prof["issue_active_pct"] / 100,
+            "inst_per_block_iteration": prof["inst_per_block_iteration"]}
 
 
 def _peaks():
@@ -386,6 +417,7 @@ def main():
         "fp32": {"achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / fp32_peak,
                  "algorithmic": f"{FLOPS_PER_COMPONENT_ITER} flop per component per iteration"},
         "kernel": "fsr_blocks_kernel<float,4,16>",
+        "counters": _counters(smem_peak),
     }
 
     line = {
@@ -399,6 +431,7 @@ def main():
                 "h2d_bytes_per_step": int(img.nbytes + mask.nbytes),
                 "d2h_bytes_per_step": int(img.nbytes)},
         "gpu_launches": args.steps,
+        "paper_context": PAPER_CONTEXT,
         "roofline": roofline,
         "clocks": clocks,
         "device": {"name": props.name, "sm_count": n_sm},
