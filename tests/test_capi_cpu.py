@@ -60,3 +60,8 @@ def test_create_rejects_bad_arguments(lib):
 
 def test_destroy_null_is_noop(lib):
     assert lib.fsr_destroy(None) == fsr.FSR_OK
+
+
+def test_status_entry_points_reject_null_handle(lib):
+    assert lib.fsr_check_status(None, None) == fsr.FSR_ERR_INVALID_ARG
+    assert lib.fsr_inject_tile_wait_fault(None) == fsr.FSR_ERR_INVALID_ARG
