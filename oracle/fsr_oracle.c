@@ -273,7 +273,7 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                              int H, int Wd, int pitch, int B, int L,
                              const fsr_oracle_params *P, long nsel,
                              const long *block_ids, int nthreads,
-                             double *out_target, int *seq, double *margin)
+                             double *out_target, double *out_im, int *seq, double *margin)
 {
     if (!img || !mask || !P || !out_target || H <= 0 || Wd <= 0 || pitch < Wd ||
         B <= 0 || L < 0 || P->S != B + 2 * L || P->K < 0)
@@ -296,6 +296,7 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
         double *f = malloc(sizeof(double) * S * S);
         unsigned char *kn = malloc((size_t)S * S);
         double *gre = malloc(sizeof(double) * S * S);
+        double *gim = out_im ? malloc(sizeof(double) * S * S) : NULL;
         unsigned char *need = calloc((size_t)S * S, 1);
         for (int a = 0; a < B; ++a)
             for (int c = 0; c < B; ++c) need[(L + a) * S + (L + c)] = 1;
@@ -312,6 +313,7 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
         o.seq = seq ? seq + s * K : NULL;
         o.margin = margin ? margin + s * K : NULL;
         o.gre = gre;
+        o.gim = gim;      /* diagnostic: Im g (the model is complex, Eq. 11) */
         o.g_need = need;  /* only the target pixels are written back */
         int r = fsr_oracle_block(P, f, kn, &o);
         if (r < 0) bad = 1;
@@ -325,8 +327,11 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                 if (y >= H || x >= Wd) val = NAN;
                 else val = kn[m * S + n] ? f[m * S + n] : gre[m * S + n];
                 out_target[(s * B + a) * B + c] = val;
+                if (out_im)
+                    out_im[(s * B + a) * B + c] =
+                        (y >= H || x >= Wd) ? NAN : (kn[m * S + n] ? 0.0 : gim[m * S + n]);
             }
-        free(f); free(kn); free(gre); free(need);
+        free(f); free(kn); free(gre); free(gim); free(need);
     }
     return bad ? -1 : n_empty;
 }

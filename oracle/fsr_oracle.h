@@ -72,6 +72,8 @@ int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
  * Block b = by * nbx + bx with nbx = ceil(Wd/B), nby = ceil(H/B).
  * block_ids: nsel indices, or NULL for all blocks in order (nsel = nbx*nby).
  * out_target: nsel*B*B reconstructed target pixels (NaN outside the image).
+ * out_im: optional nsel*B*B diagnostic, Im g at the unknown target pixels
+ *         (0 at known ones, NaN outside the image); the output is Re g.
  * seq, margin: nsel*K each, optional.
  * nthreads: OpenMP threads (<= 0: library default).
  * Returns the number of blocks without any known pixel, or -1 on error. */
@@ -79,7 +81,7 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                              int H, int Wd, int pitch, int B, int L,
                              const fsr_oracle_params *P, long nsel,
                              const long *block_ids, int nthreads,
-                             double *out_target, int *seq, double *margin);
+                             double *out_target, double *out_im, int *seq, double *margin);
 
 /* Number of OpenMP threads the image routine would use by default. */
 int fsr_oracle_max_threads(void);

@@ -78,7 +78,7 @@ class OracleLib:
             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             ctypes.POINTER(_Params), ctypes.c_long, ctypes.POINTER(ctypes.c_long),
-            ctypes.c_int, _DP, _IP, _DP]
+            ctypes.c_int, _DP, _DP, _IP, _DP]
         lib.fsr_oracle_image_blocks.restype = ctypes.c_long
         lib.fsr_oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -155,7 +155,9 @@ class OracleLib:
         """FSR of selected target blocks of an image (Sec. III-A tiling).
 
         Returns ``target`` (n, B, B) float64 (NaN outside the image), ``seq``
-        (n, K) int32, ``margin`` (n, K), ``n_empty`` and the ``block_ids`` used.
+        (n, K) int32, ``margin`` (n, K), ``n_empty``, the ``block_ids`` used
+        and ``im_target`` (n, B, B): Im g at the unknown target pixels, a
+        diagnostic of the complex model (the output is Re g; Eq. 11).
         """
         img = np.ascontiguousarray(img, np.float32)
         mask = np.ascontiguousarray(mask, np.uint8)
@@ -169,6 +171,7 @@ class OracleLib:
             ids = np.ascontiguousarray(block_ids, np.int64)
             n = ids.size
         target = np.empty((n, B, B))
+        im_target = np.empty((n, B, B))
         seq = np.empty((n, max(K, 1)), np.int32)
         margin = np.empty((n, max(K, 1)))
         P = _Params(B + 2 * L, K, rho, gamma, int(bool(freq_weight)))
@@ -177,11 +180,11 @@ class OracleLib:
             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, Wd, Wd, B, L,
             ctypes.byref(P), n,
             ids.ctypes.data_as(ctypes.POINTER(ctypes.c_long)) if ids is not None else None,
-            int(threads), _dp(target), seq.ctypes.data_as(_IP), _dp(margin))
+            int(threads), _dp(target), _dp(im_target), seq.ctypes.data_as(_IP), _dp(margin))
         if r < 0:
             raise ValueError("oracle rejected the image arguments")
         return dict(target=target, seq=seq[:, :K], margin=margin[:, :K], n_empty=int(r),
-                    block_ids=np.arange(n) if ids is None else ids)
+                    block_ids=np.arange(n) if ids is None else ids, im_target=im_target)
 
 
 def assemble_image(target: np.ndarray, H: int, Wd: int, B: int) -> np.ndarray:
