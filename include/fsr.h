@@ -147,6 +147,14 @@ int fsr_check_status(fsr_handle *h, void *stream);
  * Errors: INVALID_ARG (h NULL). */
 int fsr_inject_tile_wait_fault(fsr_handle *h);
 
+/* Blocks without any known pixel in their support (W[0][0] = 0: no
+ * iterations, g = 0, unknown target pixels written as 0; Sec. II, Eq. 10).
+ * The single-image and batch entry points of h count them on the device;
+ * this call synchronises `stream`, stores the count since the previous call
+ * in *count and resets it.  (fsr_server and fsr_reconstruct_batch_static do
+ * not count.)  Errors: INVALID_ARG (NULL h or count), CUDA. */
+int fsr_empty_blocks(fsr_handle *h, void *stream, long long *count);
+
 /* Number of target blocks N = ceil(height/B) * ceil(width/B) (Eq. 13);
  * 0 for invalid sizes. */
 long long fsr_num_blocks(int height, int width, int block);

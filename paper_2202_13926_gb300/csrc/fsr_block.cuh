@@ -84,6 +84,7 @@ struct KernelArgs {
     long long nblocks;   // N
     MethodArgs mth;
     unsigned* status;    // device status word (kStatus* bits)
+    unsigned long long* empty;   // optional: += blocks without a known pixel
     int tiles;           // 1: support tiles by TMA through `maps`; 0: plain loads
     int tx_extra;        // test hook: extra bytes each tile wait expects (0 in use)
     TileMaps maps;
@@ -99,6 +100,7 @@ struct BatchArgs {
     unsigned long long* counter; // zero at launch
     int chunk;                   // blocks taken per counter increment
     MethodArgs mth;
+    unsigned long long* empty = nullptr;   // optional: += blocks without a known pixel
 };
 
 // cos(pi t / 16) for t = 0..8 (mathematical constants).
@@ -1073,6 +1075,14 @@ __device__ __forceinline__ void dense_inverse_targets(const float2* gd, typename
     __syncwarp();
 }
 
+// A support without a known pixel: no iterations (g = 0), the selection
+// sequence is -1, and the block is counted (reading: W[0][0] = 0).
+__device__ __forceinline__ void empty_block(int16_t* seq, int K, unsigned long long* empty) {
+    if (seq != nullptr)
+        for (int nu = 0; nu < K; ++nu) seq[nu] = -1;
+    if (empty != nullptr) atomicAdd(empty, 1ull);
+}
+
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
 // With a tile context the support comes in by TMA; returns false when the
 // bounded wait for it gave up (the warp then stops taking blocks).
@@ -1080,7 +1090,8 @@ template <typename T, int B, Dft DFT = Dft::SIMT>
 __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
-                                              const unsigned char* tctab, const TileReq& tr, int lane) {
+                                              const unsigned char* tctab, const TileReq& tr,
+                                              unsigned long long* empty, int lane) {
     constexpr int P = TargetPix<B>::P;
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -1119,15 +1130,15 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
         if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
             iterate<B, true>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc, gd);
             dense_inverse_targets<B, DFT>(gd, Wd, rowbuf, tctab, lane, zr, zi, gacc);
-        } else if (seq != nullptr && lane == 0) {
-            for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+        } else if (lane == 0) {
+            empty_block(seq, im.K, empty);
         }
     } else {
         if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
             iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
             __syncwarp();   // W area free for the next block
-        } else if (seq != nullptr && lane == 0) {
-            for (int nu = 0; nu < im.K; ++nu) seq[nu] = -1;
+        } else if (lane == 0) {
+            empty_block(seq, im.K, empty);
         }
     }
 
@@ -1191,7 +1202,8 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
         tr.bytes = kTileBytes + (unsigned)a.tx_extra;
         tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * wq);
         tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + wq;
-        if (!process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, tr, lane))
+        if (!process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, tr, a.empty,
+                                      lane))
             break;
     }
 }
@@ -1232,7 +1244,7 @@ fsr_batch_kernel(const BatchArgs a) {
             }
             const ImageArgs im = a.images[lo];
             process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
-                                rowbuf, nullptr, TileReq{nullptr, nullptr, 0u, 0u, nullptr}, lane);
+                                rowbuf, nullptr, TileReq{nullptr, nullptr, 0u, 0u, nullptr}, a.empty, lane);
         }
     }
 }

@@ -203,6 +203,7 @@ int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int hei
     a.nblocks = (long long)a.im.nbx * ((height + p->block - 1) / p->block);
     a.mth = method_args(p);
     a.status = h->d_status;
+    a.empty = h->d_empty;
     if (tiles_possible(img, mask, pitch)) {
         const int r = encode_tile_maps(h, img, mask, height, width, pitch, &a.maps);
         if (r != FSR_OK) return r;
@@ -348,7 +349,8 @@ int make_plan(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p
         delete b;
         return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
     }
-    const fsrk::BatchArgs a = batch_args(b->d_table, n, total, p, sc.chunk);
+    fsrk::BatchArgs a = batch_args(b->d_table, n, total, p, sc.chunk);
+    a.empty = h->d_empty;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t el = launch_batch(a, p, sc, h->sm_count, cs);
@@ -408,14 +410,15 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
         delete h;
         return fail(nullptr, FSR_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
     }
-    if ((e = cudaMalloc(&h->d_status, sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMemset(h->d_status, 0, sizeof(unsigned))) != cudaSuccess) {
+    // status word (bytes 0..3) and empty-block counter (bytes 8..15)
+    if ((e = cudaMalloc(&h->d_status, 16)) != cudaSuccess || (e = cudaMemset(h->d_status, 0, 16)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->d_status);
         cudaEventDestroy(h->table_free);
         delete h;
         return fail(nullptr, FSR_ERR_OOM, "device status word: %s", cudaGetErrorString(e));
     }
+    h->d_empty = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->d_status) + 8);
     h->device = cfg->device;
     h->sm_count = prop.multiProcessorCount;
     snprintf(h->device_name, sizeof h->device_name, "%s", prop.name);
@@ -529,6 +532,20 @@ int fsr_check_status(fsr_handle* h, void* stream) {
     return read_status(h);
 }
 
+int fsr_empty_blocks(fsr_handle* h, void* stream, long long* count) {
+    if (!h || !count) return fail(h, FSR_ERR_INVALID_ARG, "handle or count is NULL");
+    DeviceGuard g;
+    cudaError_t e = g.set(h->device);
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    unsigned long long c = 0;
+    if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess ||
+        (e = cudaMemcpy(&c, h->d_empty, sizeof c, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemset(h->d_empty, 0, sizeof c)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "reading the empty-block counter: %s", cudaGetErrorString(e));
+    *count = (long long)c;
+    return ok(h);
+}
+
 int fsr_inject_tile_wait_fault(fsr_handle* h) {
     if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
     h->inject_tile_fault = 1;
@@ -572,7 +589,9 @@ int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const f
     const fsrk::Schedule sc = h->sched[p->precision][b_index(p->block)];
     if ((e = cudaMemcpyAsync(h->d_table, h->h_table, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
-    if ((e = launch_batch(batch_args(h->d_table, n, total, p, sc.chunk), p, sc, h->sm_count, s)) != cudaSuccess)
+    fsrk::BatchArgs ba = batch_args(h->d_table, n, total, p, sc.chunk);
+    ba.empty = h->d_empty;
+    if ((e = launch_batch(ba, p, sc, h->sm_count, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
     if ((e = cudaEventRecord(h->table_free, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));

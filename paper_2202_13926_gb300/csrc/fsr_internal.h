@@ -52,5 +52,6 @@ struct fsr_handle {
     cudaEvent_t table_free = nullptr;
     // device status word of the single-image kernels (fsrk::kStatus* bits)
     unsigned* d_status = nullptr;
+    unsigned long long* d_empty = nullptr;   // blocks without a known pixel (inside the status allocation)
     int inject_tile_fault = 0;     // test hook: next tile-copy launch waits for bytes that never come
 };

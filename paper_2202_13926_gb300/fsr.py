@@ -37,7 +37,7 @@ EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
             "fsr_autotune_batch", "fsr_get_schedule", "fsr_set_schedule",
             "fsr_reconstruct_batch_static", "fsr_server_create", "fsr_server_submit",
             "fsr_server_poll", "fsr_server_stats", "fsr_server_destroy",
-            "fsr_check_status", "fsr_inject_tile_wait_fault")
+            "fsr_check_status", "fsr_inject_tile_wait_fault", "fsr_empty_blocks")
 
 
 class FsrError(RuntimeError):
@@ -126,12 +126,14 @@ def load_library(path: str | None = None):
         lib.fsr_server_destroy.argtypes = [vp]
         lib.fsr_check_status.argtypes = [vp, vp]
         lib.fsr_inject_tile_wait_fault.argtypes = [vp]
+        lib.fsr_empty_blocks.argtypes = [vp, vp, llp]
         for name in ("fsr_server_create", "fsr_server_submit", "fsr_server_poll",
                      "fsr_server_stats", "fsr_server_destroy"):
             getattr(lib, name).restype = ip
         for name in ("fsr_reconstruct_batch_static", "fsr_reconstruct_batch", "fsr_batch_create", "fsr_batch_launch",
                      "fsr_batch_destroy", "fsr_autotune_batch", "fsr_get_schedule",
-                     "fsr_set_schedule", "fsr_check_status", "fsr_inject_tile_wait_fault"):
+                     "fsr_set_schedule", "fsr_check_status", "fsr_inject_tile_wait_fault",
+                     "fsr_empty_blocks"):
             getattr(lib, name).restype = ip
         if path is None:
             _lib = lib
@@ -243,6 +245,14 @@ def fsr_check_status(handle, stream=None) -> None:
     """Synchronise ``stream`` and raise FsrError(FSR_ERR_TIMEOUT) when a
     bounded tile-copy wait of a single-image launch gave up."""
     _check(load_library().fsr_check_status(handle, _stream_ptr(stream)), handle)
+
+
+def fsr_empty_blocks(handle, stream=None) -> int:
+    """Synchronise ``stream``; number of blocks without a known pixel since
+    the previous call (the counter is reset)."""
+    c = ctypes.c_longlong()
+    _check(load_library().fsr_empty_blocks(handle, _stream_ptr(stream), ctypes.byref(c)), handle)
+    return c.value
 
 
 def fsr_inject_tile_wait_fault(handle) -> None:

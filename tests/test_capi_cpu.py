@@ -65,3 +65,5 @@ def test_destroy_null_is_noop(lib):
 def test_status_entry_points_reject_null_handle(lib):
     assert lib.fsr_check_status(None, None) == fsr.FSR_ERR_INVALID_ARG
     assert lib.fsr_inject_tile_wait_fault(None) == fsr.FSR_ERR_INVALID_ARG
+    c = ctypes.c_longlong()
+    assert lib.fsr_empty_blocks(None, None, ctypes.byref(c)) == fsr.FSR_ERR_INVALID_ARG

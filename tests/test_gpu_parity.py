@@ -182,3 +182,24 @@ def test_fhd_quarter_full_frame(handle):
     print(f"fhd: within 0.5 {frac:.5f}, dPSNR {dpsnr:.5f} dB, identical sequences {same:.4f}")
     assert frac >= PA.FRAC_MIN, frac
     assert dpsnr <= PA.PSNR_TOL_DB, dpsnr
+
+
+def test_empty_blocks_are_counted_like_the_oracle(handle):
+    """Supports without any known pixel (W[0][0] = 0) are counted on the
+    device; the count equals the oracle's, for the FP32 and FP64 single-image
+    kernels and for the batch kernel."""
+    from paper_2202_13926_gb300 import fsr
+    H, W = 100, 140
+    img = synth.sinusoid_image(H, W, seed=41)
+    m = synth.macroblock_mask(H, W, seed=42, lost=0.6, mb=40)
+    n_ref = oracle.fsr_image_blocks(img, m, K=10)["n_empty"]
+    assert n_ref > 0
+    fsr.fsr_empty_blocks(handle.ptr)                       # reset
+    for prec in ("fp32", "fp64"):
+        run_gpu(handle, img, m, iters=10, precision=prec)
+        assert fsr.fsr_empty_blocks(handle.ptr) == n_ref, prec
+    dev = torch.device("cuda:0")
+    ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(m).to(dev)
+    to = torch.empty_like(ti)
+    fsr.fsr_reconstruct_batch(handle.ptr, [fsr.image_desc(ti, tm, to, 10)], fsr.make_params(iters=10))
+    assert fsr.fsr_empty_blocks(handle.ptr) == n_ref
