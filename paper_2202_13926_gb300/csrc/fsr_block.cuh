@@ -52,6 +52,7 @@ struct ImageArgs {
     int H, W, pitch;     // geometry (pitch in elements, shared by img, mask, out)
     int nbx;             // ceil(W / B): blocks per block row
     int K;               // iterations of this image
+    int tiles;           // batch form: 1 = maps[image] holds this image's tile descriptors
 };
 
 // Parameters shared by every image of a launch.
@@ -78,10 +79,11 @@ struct TileMaps {
 // Device status word bits (set by kernels, read and cleared by the host).
 constexpr unsigned kStatusTileWait = 1u;   // a bounded wait on a tile copy gave up
 
-// Single image, static schedule.
+// Single image: warps take blocks one at a time from a device work counter.
 struct KernelArgs {
     ImageArgs im;
     long long nblocks;   // N
+    unsigned long long* work;   // [next block, finished warps]: zero at launch; the last warp resets both
     MethodArgs mth;
     unsigned* status;    // device status word (kStatus* bits)
     unsigned long long* empty;   // optional: += blocks without a known pixel
@@ -92,6 +94,7 @@ struct KernelArgs {
 
 // Many images, dynamic schedule: warps take chunks of the concatenated block
 // list (images ordered by decreasing K) from a device counter.
+struct TileMaps;
 struct BatchArgs {
     const ImageArgs* images;     // n images, device memory
     const long long* first;      // n + 1 prefix sums of the block counts
@@ -101,6 +104,9 @@ struct BatchArgs {
     int chunk;                   // blocks taken per counter increment
     MethodArgs mth;
     unsigned long long* empty = nullptr;   // optional: += blocks without a known pixel
+    const TileMaps* maps = nullptr;        // optional: n tile descriptors (device, 64-byte aligned)
+    unsigned* status = nullptr;            // device status word (needed with maps)
+    int tx_extra = 0;                      // test hook of the tile wait (0 in use)
 };
 
 // cos(pi t / 16) for t = 0..8 (mathematical constants).
@@ -1193,8 +1199,11 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
     }
 
     const T gamma = T(a.mth.gamma);
-    for (long long blk = (long long)blockIdx.x * WARPS + warp; blk < a.nblocks;
-         blk += (long long)gridDim.x * WARPS) {
+    for (;;) {
+        unsigned long long next = 0;
+        if (lane == 0) next = atomicAdd(a.work, 1ull);
+        const long long blk = (long long)__shfl_sync(FULL, next, 0);
+        if (blk >= a.nblocks) break;
         const int wq = threadIdx.x >> 5;
         TileReq tr;
         tr.maps = tiles ? &a.maps : nullptr;
@@ -1205,6 +1214,14 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
         if (!process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, tr, a.empty,
                                       lane))
             break;
+    }
+    // the last warp of the launch leaves the counter at zero for the next one
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(a.work + 1, 1ull) == (unsigned long long)gridDim.x * WARPS - 1) {
+            atomicExch(a.work, 0ull);
+            atomicExch(a.work + 1, 0ull);
+        }
     }
 }
 
@@ -1227,6 +1244,16 @@ fsr_batch_kernel(const BatchArgs a) {
     cta_tables<T>(a.mth, sw0, swf, scs);
     __syncthreads();
 
+    // tile copies need 128-byte aligned destinations (kept by the layout)
+    const bool tiles = a.maps != nullptr && (smem_addr(smem) & 127u) == 0;
+    if (tiles) {
+        if (lane == 0) {
+            tile_bar_init(smem_addr(smem + Lay::bar_off(WARPS) + 8 * warp));
+            reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS))[warp] = 0;
+        }
+        __syncwarp();
+    }
+
     const T gamma = T(a.mth.gamma);
     for (;;) {
         unsigned long long base = 0;
@@ -1234,7 +1261,8 @@ fsr_batch_kernel(const BatchArgs a) {
         base = __shfl_sync(FULL, base, 0);
         if (base >= (unsigned long long)a.total) break;
         const long long end = min((long long)base + a.chunk, a.total);
-        for (long long item = (long long)base; item < end; ++item) {
+        bool ok = true;
+        for (long long item = (long long)base; item < end && ok; ++item) {
             // image of this entry: last i with first[i] <= item
             int lo = 0, hi = a.n - 1;
             while (lo < hi) {
@@ -1243,9 +1271,16 @@ fsr_batch_kernel(const BatchArgs a) {
                 else hi = mid - 1;
             }
             const ImageArgs im = a.images[lo];
-            process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
-                                rowbuf, nullptr, TileReq{nullptr, nullptr, 0u, 0u, nullptr}, a.empty, lane);
+            TileReq tr;
+            tr.maps = (tiles && im.tiles) ? a.maps + lo : nullptr;
+            tr.status = a.status;
+            tr.bytes = kTileBytes + (unsigned)a.tx_extra;
+            tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * warp);
+            tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + warp;
+            ok = process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf,
+                                     nullptr, tr, a.empty, lane);
         }
+        if (!ok) break;   // a tile wait gave up: this warp takes no more blocks
     }
 }
 

@@ -125,6 +125,7 @@ fsrk::ImageArgs image_args(const float* img, const uint8_t* mask, float* out, in
     im.pitch = pitch;
     im.nbx = (width + B - 1) / B;
     im.K = iters;
+    im.tiles = 0;
     return im;
 }
 
@@ -195,8 +196,46 @@ int read_status(fsr_handle* h) {
                 st);
 }
 
+// FP32 single image: a one-image work table in one of the handle's table
+// slots (used in turn; a slot is reused once the launch that read it has
+// finished), then the batch kernel with the handle's FP32 schedule.
+int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                        const fsr_params* p, float* out, cudaStream_t stream) {
+    const int slot = (int)(h->single_next++ % fsr_handle::kSingleSlots);
+    cudaError_t e;
+    if (h->single_used[slot] && (e = cudaEventSynchronize(h->single_ev[slot])) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "waiting for a table slot: %s", cudaGetErrorString(e));
+    char* host = static_cast<char*>(h->h_single) + (size_t)slot * fsr_handle::kSingleSlotBytes;
+    char* dev = static_cast<char*>(h->d_single) + (size_t)slot * fsr_handle::kSingleSlotBytes;
+    fsr_image_desc d;
+    d.img = img;
+    d.mask = mask;
+    d.out = out;
+    d.seq_out = p->seq_out;
+    d.height = height;
+    d.width = width;
+    d.pitch = pitch;
+    d.iters = p->iters;
+    const long long total = build_table(h, 1, &d, p, host);
+    if (total < 0) return FSR_ERR_CUDA;
+    if ((e = cudaMemcpyAsync(dev, host, table_bytes(1), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+    const fsrk::Schedule sc = h->sched[FSR_FP32][b_index(p->block)];
+    fsrk::BatchArgs a = batch_args(h, dev, 1, total, p, sc.chunk);
+    a.empty = h->d_empty;
+    a.tx_extra = h->inject_tile_fault ? 16 : 0;
+    h->inject_tile_fault = 0;
+    if ((e = fsrk::launch_batch_fp32(a, p->block, sc, h->sm_count, stream)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    if ((e = cudaEventRecord(h->single_ev[slot], stream)) != cudaSuccess)
+        return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    h->single_used[slot] = true;
+    return ok(h);
+}
+
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                    const fsr_params* p, float* out, cudaStream_t stream) {
+    if (p->precision == FSR_FP32) return enqueue_single_fp32(h, img, mask, height, width, pitch, p, out, stream);
     fsrk::KernelArgs a;
     std::memset(&a, 0, sizeof a);
     a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
@@ -204,6 +243,7 @@ int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int hei
     a.mth = method_args(p);
     a.status = h->d_status;
     a.empty = h->d_empty;
+    a.work = h->d_work + 2 * (h->work_next++ % fsr_handle::kWorkSlots);
     if (tiles_possible(img, mask, pitch)) {
         const int r = encode_tile_maps(h, img, mask, height, width, pitch, &a.maps);
         if (r != FSR_OK) return r;
@@ -213,21 +253,22 @@ int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int hei
     }
     cudaError_t e;
     if (p->precision == FSR_FP64_DEBUG) e = fsrk::launch_single_fp64(a, p->block, h->sm_count, stream);
-    else if (p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32)
-        e = fsrk::launch_single_fp32_tc(a, p->block, p->precision == FSR_TC_BF16X3, h->sm_count, stream);
-    else e = fsrk::launch_single_fp32(a, p->block, h->sm_count, stream);
+    else e = fsrk::launch_single_fp32_tc(a, p->block, p->precision == FSR_TC_BF16X3, h->sm_count, stream);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return ok(h);
 }
 
 // ---- batch work tables -----------------------------------------------------
-// Layout in one device allocation: [counter u64][first: (n+1) x i64][images: n x ImageArgs]
+// Layout in one device allocation: [counter u64][first: (n+1) x i64] (padded
+// to 16 B) [images: n x ImageArgs] (padded to 128 B) [maps: n x TileMaps].
 
-size_t table_bytes(int n) {
-    size_t b = sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1);
-    b = (b + 15) & ~(size_t)15;
-    return b + sizeof(fsrk::ImageArgs) * (size_t)n;
+size_t images_off(int n) {
+    return (sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1) + 15) & ~(size_t)15;
 }
+
+size_t maps_off(int n) { return (images_off(n) + sizeof(fsrk::ImageArgs) * (size_t)n + 127) & ~(size_t)127; }
+
+size_t table_bytes(int n) { return maps_off(n) + sizeof(fsrk::TileMaps) * (size_t)n; }
 
 int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p) {
     if (n < 1) return fail(h, FSR_ERR_INVALID_ARG, "batch needs n >= 1 images (got %d)", n);
@@ -244,20 +285,26 @@ int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params*
 }
 
 // Fill the host image of the table; returns the total number of blocks.
-long long build_table(int n, const fsr_image_desc* d, const fsr_params* p, void* host) {
+long long build_table(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p, void* host) {
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a].iters > d[b].iters; });
     char* base = static_cast<char*>(host);
     auto* counter = reinterpret_cast<unsigned long long*>(base);
     auto* first = reinterpret_cast<long long*>(base + sizeof(unsigned long long));
-    size_t off = (sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1) + 15) & ~(size_t)15;
-    auto* imgs = reinterpret_cast<fsrk::ImageArgs*>(base + off);
+    auto* imgs = reinterpret_cast<fsrk::ImageArgs*>(base + images_off(n));
+    char* maps = base + maps_off(n);
     *counter = 0;
     long long total = 0;
     for (int j = 0; j < n; ++j) {
         const fsr_image_desc& x = d[order[j]];
         imgs[j] = image_args(x.img, x.mask, x.out, x.seq_out, x.height, x.width, x.pitch, x.iters, p->block);
+        if (tiles_possible(x.img, x.mask, x.pitch)) {
+            fsrk::TileMaps tm;   // encoded at its own alignment, then copied into the table
+            if (encode_tile_maps(h, x.img, x.mask, x.height, x.width, x.pitch, &tm) != FSR_OK) return -1;
+            std::memcpy(maps + sizeof(fsrk::TileMaps) * (size_t)j, &tm, sizeof tm);
+            imgs[j].tiles = 1;
+        }
         first[j] = total;
         total += fsr_num_blocks(x.height, x.width, p->block);
     }
@@ -265,13 +312,14 @@ long long build_table(int n, const fsr_image_desc* d, const fsr_params* p, void*
     return total;
 }
 
-fsrk::BatchArgs batch_args(void* d_table, int n, long long total, const fsr_params* p, int chunk) {
+fsrk::BatchArgs batch_args(fsr_handle* h, void* d_table, int n, long long total, const fsr_params* p, int chunk) {
     char* base = static_cast<char*>(d_table);
-    size_t off = (sizeof(unsigned long long) + sizeof(long long) * (size_t)(n + 1) + 15) & ~(size_t)15;
     fsrk::BatchArgs a;
     a.counter = reinterpret_cast<unsigned long long*>(base);
     a.first = reinterpret_cast<const long long*>(base + sizeof(unsigned long long));
-    a.images = reinterpret_cast<const fsrk::ImageArgs*>(base + off);
+    a.images = reinterpret_cast<const fsrk::ImageArgs*>(base + images_off(n));
+    a.maps = reinterpret_cast<const fsrk::TileMaps*>(base + maps_off(n));
+    a.status = h->d_status;
     a.n = n;
     a.total = total;
     a.chunk = chunk;
@@ -331,7 +379,8 @@ int make_plan(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p
     if (h->ws_cap && h->ws_used + bytes > h->ws_cap)
         return fail(h, FSR_ERR_OOM, "batch table of %zu bytes exceeds the workspace cap of %zu", bytes, h->ws_cap);
     std::vector<char> host(bytes);
-    const long long total = build_table(n, d, p, host.data());
+    const long long total = build_table(h, n, d, p, host.data());
+    if (total < 0) return FSR_ERR_CUDA;
     fsr_batch* b = new (std::nothrow) fsr_batch();
     if (!b) return fail(h, FSR_ERR_OOM, "host allocation of the batch failed");
     b->h = h;
@@ -349,7 +398,7 @@ int make_plan(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params* p
         delete b;
         return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
     }
-    fsrk::BatchArgs a = batch_args(b->d_table, n, total, p, sc.chunk);
+    fsrk::BatchArgs a = batch_args(h, b->d_table, n, total, p, sc.chunk);
     a.empty = h->d_empty;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -400,7 +449,7 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
     if (!(prop.major == 10 && prop.minor == 3))
         return fail(nullptr, FSR_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only",
                     cfg->device, prop.major, prop.minor);
-    if ((e = fsrk::configure_fp32()) != cudaSuccess || (e = fsrk::configure_fp32_batch()) != cudaSuccess ||
+    if ((e = fsrk::configure_fp32_batch()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
         (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));
@@ -410,15 +459,42 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
         delete h;
         return fail(nullptr, FSR_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
     }
-    // status word (bytes 0..3) and empty-block counter (bytes 8..15)
-    if ((e = cudaMalloc(&h->d_status, 16)) != cudaSuccess || (e = cudaMemset(h->d_status, 0, 16)) != cudaSuccess) {
+    // status word (bytes 0..3), empty-block counter (bytes 8..15), then the
+    // work counters of the single-image launches (kWorkSlots x 16 B)
+    const size_t sbytes = 16 + 16 * (size_t)fsr_handle::kWorkSlots;
+    if ((e = cudaMalloc(&h->d_status, sbytes)) != cudaSuccess ||
+        (e = cudaMemset(h->d_status, 0, sbytes)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->d_status);
         cudaEventDestroy(h->table_free);
         delete h;
         return fail(nullptr, FSR_ERR_OOM, "device status word: %s", cudaGetErrorString(e));
     }
+    if (table_bytes(1) > fsr_handle::kSingleSlotBytes) {
+        cudaFree(h->d_status);
+        cudaEventDestroy(h->table_free);
+        delete h;
+        return fail(nullptr, FSR_ERR_UNSUPPORTED, "internal: one-image table larger than its slot");
+    }
+    {
+        const size_t sb = fsr_handle::kSingleSlotBytes * fsr_handle::kSingleSlots;
+        bool okay = cudaMalloc(&h->d_single, sb) == cudaSuccess && cudaMallocHost(&h->h_single, sb) == cudaSuccess;
+        for (int i = 0; okay && i < fsr_handle::kSingleSlots; ++i)
+            okay = cudaEventCreateWithFlags(&h->single_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!okay) {
+            cudaGetLastError();
+            for (cudaEvent_t ev : h->single_ev)
+                if (ev) cudaEventDestroy(ev);
+            cudaFree(h->d_single);
+            if (h->h_single) cudaFreeHost(h->h_single);
+            cudaFree(h->d_status);
+            cudaEventDestroy(h->table_free);
+            delete h;
+            return fail(nullptr, FSR_ERR_OOM, "allocating the single-image table slots failed");
+        }
+    }
     h->d_empty = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->d_status) + 8);
+    h->d_work = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->d_status) + 16);
     h->device = cfg->device;
     h->sm_count = prop.multiProcessorCount;
     snprintf(h->device_name, sizeof h->device_name, "%s", prop.name);
@@ -440,6 +516,10 @@ int fsr_destroy(fsr_handle* h) {
             cudaFree(h->d_out);
             cudaFree(h->d_table);
             cudaFree(h->d_status);
+            cudaFree(h->d_single);
+            if (h->h_single) cudaFreeHost(h->h_single);
+            for (cudaEvent_t ev : h->single_ev)
+                if (ev) cudaEventDestroy(ev);
             if (h->h_table) cudaFreeHost(h->h_table);
             if (h->table_free) cudaEventDestroy(h->table_free);
         }
@@ -575,7 +655,6 @@ int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const f
         if (cudaMalloc(&h->d_table, bytes) != cudaSuccess || cudaMallocHost(&h->h_table, bytes) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(h->d_table);
-            cudaFree(h->d_status);
             if (h->h_table) cudaFreeHost(h->h_table);
             h->d_table = nullptr;
             h->h_table = nullptr;
@@ -584,12 +663,13 @@ int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const f
         h->table_bytes = bytes;
         h->ws_used += bytes;
     }
-    const long long total = build_table(n, d, p, h->h_table);
+    const long long total = build_table(h, n, d, p, h->h_table);
+    if (total < 0) return FSR_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const fsrk::Schedule sc = h->sched[p->precision][b_index(p->block)];
     if ((e = cudaMemcpyAsync(h->d_table, h->h_table, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
-    fsrk::BatchArgs ba = batch_args(h->d_table, n, total, p, sc.chunk);
+    fsrk::BatchArgs ba = batch_args(h, h->d_table, n, total, p, sc.chunk);
     ba.empty = h->d_empty;
     if ((e = launch_batch(ba, p, sc, h->sm_count, s)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
@@ -661,7 +741,7 @@ int fsr_autotune_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_
     if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "autotune setup: %s", cudaGetErrorString(e));
-    const int warps_c[3] = {16, 12, 8};
+    const int warps_c[3] = {fsrk::kWarpsFp32, 12, 16};
     const int chunk_c[4] = {1, 2, 4, 8};
     fsrk::Schedule win = h->sched[p->precision][b_index(p->block)];
     float win_ms = -1.f;

@@ -9,6 +9,10 @@
 
 namespace fsrk {
 
+// Warps per CTA of the default FP32 batch kernels (which also run every FP32
+// single-image call): two CTAs of 8 warps per SM.
+constexpr int kWarpsFp32 = 8;
+
 // A persistent schedule: warps per CTA (one support block per warp) and the
 // number of blocks a warp takes per work-counter increment (batch form).
 struct Schedule {
@@ -18,17 +22,15 @@ struct Schedule {
 
 // Sets the dynamic shared-memory limit of every instantiation of the family;
 // call once per device with that device current.
-cudaError_t configure_fp32();
 cudaError_t configure_fp32_batch();
 cudaError_t configure_fp32_sched();
 cudaError_t configure_fp64();
 cudaError_t configure_fp64_batch();
 cudaError_t configure_fp32_tc();
 
-// Single image, static schedule, 16 (FP32) or 4 (FP64) warps per CTA.
-cudaError_t launch_single_fp32(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
+// Single image (FP64 debug, 4 warps per CTA): warps take blocks from a work counter.
 cudaError_t launch_single_fp64(const KernelArgs& a, int B, int sm_count, cudaStream_t stream);
-// Forward transform on tensor cores (TF32, or BF16 hi/lo with bf16x3 = 1); B = 4 only.
+// Both 2-D DFTs on tensor cores (TF32, or BF16 hi/lo with bf16x3 = 1); B = 4 only.
 cudaError_t launch_single_fp32_tc(const KernelArgs& a, int B, int bf16x3, int sm_count, cudaStream_t stream);
 
 // Batch form.  Returns cudaErrorNotSupported for a schedule that is not
@@ -37,8 +39,8 @@ cudaError_t launch_batch_fp32(const BatchArgs& a, int B, Schedule sc, int sm_cou
 cudaError_t launch_batch_fp32_sched(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 cudaError_t launch_batch_fp64(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 
-// Warps-per-CTA values instantiated for (precision, B): FP32 has 16 for every
-// B and also 8 and 12 for B = 4; FP64 has 4.
+// Warps-per-CTA values instantiated for (precision, B): FP32 has 8 for every
+// B and also 12 and 16 for B = 4; FP64 has 4.
 bool batch_schedule_supported(int fp64, int B, int warps);
 
 // Persistent grid: resident CTAs per SM x SMs, capped by the work available.

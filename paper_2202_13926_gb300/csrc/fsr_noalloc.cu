@@ -156,7 +156,7 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
     ba.mth.rho = p->rho;
     ba.mth.gamma = p->gamma;
     ba.mth.freq_weight = p->freq_weight;
-    const fsrk::Schedule sc{p->precision == FSR_FP64_DEBUG ? 4 : 16, 1};
+    const fsrk::Schedule sc{p->precision == FSR_FP64_DEBUG ? 4 : fsrk::kWarpsFp32, 1};
     e = (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(ba, p->block, sc, su.sm_count, s)
                                          : fsrk::launch_batch_fp32(ba, p->block, sc, su.sm_count, s);
     if (e != cudaSuccess) return report(err, err_len, FSR_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));

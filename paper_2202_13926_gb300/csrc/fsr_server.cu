@@ -258,16 +258,17 @@ bool step(fsr_server* s) {
                     d[j].iters = r->K;
                     d[j].seq_out = nullptr;
                 }
-                const long long total = fsri::build_table(n, d.data(), &s->p, s->h_tables[slot]);
+                const long long total = fsri::build_table(s->h, n, d.data(), &s->p, s->h_tables[slot]);
                 cudaStream_t cs = s->s_comp[slot];
-                cudaError_t e = cudaSuccess;
+                cudaError_t e = total < 0 ? cudaErrorInvalidValue : cudaSuccess;
                 for (Request* r : batch)
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, r->ev, 0);
                 void* dt = s->pool + toff;
                 if (e == cudaSuccess) e = cudaMemcpyAsync(dt, s->h_tables[slot], tbytes, cudaMemcpyHostToDevice, cs);
                 const fsrk::Schedule sc = s->h->sched[s->p.precision][fsri::b_index(s->p.block)];
                 if (e == cudaSuccess)
-                    e = fsri::launch_batch(fsri::batch_args(dt, n, total, &s->p, sc.chunk), &s->p, sc, s->h->sm_count, cs);
+                    e = fsri::launch_batch(fsri::batch_args(s->h, dt, n, total, &s->p, sc.chunk), &s->p, sc,
+                                           s->h->sm_count, cs);
                 if (e == cudaSuccess) e = cudaEventRecord(L.done, cs);
                 if (e != cudaSuccess) {
                     cudaGetLastError();

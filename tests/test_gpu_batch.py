@@ -131,7 +131,7 @@ def test_every_schedule_gives_identical_results(fsr_mod, handle):
     finally:
         fsr.fsr_set_schedule(handle.ptr, *saved)
     with pytest.raises(fsr.FsrError) as e:
-        fsr.fsr_set_schedule(handle.ptr, 8, 1, block=8)   # not instantiated for B = 8
+        fsr.fsr_set_schedule(handle.ptr, 12, 1, block=8)   # not instantiated for B = 8
     assert e.value.code == fsr.FSR_ERR_UNSUPPORTED
 
 
