@@ -85,7 +85,10 @@ def _profile():
         prof = json.load(fh)
     m = hashlib.sha256()
     for src in prof.get("kernel_sources", []):
-        with open(os.path.join(ROOT, src), "rb") as fh:
+        path = os.path.join(ROOT, src)
+        if not os.path.exists(path):
+            return None
+        with open(path, "rb") as fh:
             m.update(fh.read())
     if m.hexdigest() != prof.get("kernel_source_sha256"):
         return None
