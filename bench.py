@@ -78,7 +78,7 @@ def _profile():
     """The committed ncu summary of the top kernel, or None when the kernel
     sources changed since that capture."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "fsr_blocks_kernel_fp32_1080p_K100.json")
+    p = os.path.join(ROOT, "profiles", "fsr_batch_kernel_fp32_1080p_K100.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
@@ -109,7 +109,7 @@ def _counters(smem_peak_gbs):
         return None
     dur = prof["duration_ms"] * 1e-3
     smem_gbs = prof["smem_wavefronts"] * 128 / dur / 1e9
-    return {"source": "profiles/fsr_blocks_kernel_fp32_1080p_K100.json (ncu --set full, one launch)",
+    return {"source": "profiles/fsr_batch_kernel_fp32_1080p_K100.json (ncu --set full, one launch)",
             "duration_ms": dur * 1e3,
             "smem_pipe_gbs": smem_gbs, "smem_pipe_frac": smem_gbs / smem_peak_gbs,
             "smem_note": "all shared-memory wavefronts x 128 B (W stream, tile, transposes, publication, conflicts)",
@@ -471,7 +471,7 @@ def main():
     roofline = {
         "bound": "smem", "achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s",
         "frac": smem_gbs / smem_peak, "traffic": _profiled_traffic(),
-        "traffic_note": "DRAM bytes per launch from profiles/fsr_blocks_kernel_fp32_1080p_K100.json "
+        "traffic_note": "DRAM bytes per launch from profiles/fsr_batch_kernel_fp32_1080p_K100.json "
                         "(inputs are L2 resident; null when the kernel changed since the capture)",
         "peak_source": f"derived: {n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_max:.0f} MHz (max SM clock)",
         "algorithmic": f"{W_BYTES_PER_COMPONENT_ITER} B of W per component per iteration, "
