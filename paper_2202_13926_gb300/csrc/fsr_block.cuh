@@ -829,12 +829,20 @@ __device__ __forceinline__ Pick argmax_pick(const float (&zr)[S], const float (&
                                             float ar, float ai, int lane) {
     const float m = groups_max(g);
     const unsigned Mb = __reduce_max_sync(FULL, __float_as_uint(m));
-    const int u = __ffs(__ballot_sync(FULL, __float_as_uint(m) == Mb)) - 1;
-    // first group of this lane's row that holds the maximum (used from lane u)
-    int jg = NG - 1;
+    const unsigned bu = __ballot_sync(FULL, __float_as_uint(m) == Mb);
+    const int u = __ffs(bu) - 1;
+    // first group of lane u's row that holds the maximum
+    int jg;
+    if constexpr (NG == 2) {
+        // a second ballot, independent of u: bit u says whether group 0 holds it
+        const unsigned b0 = __ballot_sync(FULL, __float_as_uint(g[0]) == Mb);
+        jg = ((b0 >> u) & 1u) ? 0 : 1;
+    } else {
+        jg = NG - 1;
 #pragma unroll
-    for (int j = NG - 2; j >= 0; --j) jg = (__float_as_uint(g[j]) == Mb) ? j : jg;
-    jg = __shfl_sync(FULL, jg, u);
+        for (int j = NG - 2; j >= 0; --j) jg = (__float_as_uint(g[j]) == Mb) ? j : jg;
+        jg = __shfl_sync(FULL, jg, u);
+    }
     publish_group(zr, zi, jg, lane == u, rowbuf);
     __syncwarp();
     const int cl = GS * jg + (lane & (GS - 1));   // column examined by this lane
