@@ -260,6 +260,21 @@ def _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torc
     return {"points": rows, "ms_per_iteration": per_iter, "prologue_ms": rows[0]["ms_per_frame"]}
 
 
+def _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch):
+    """Reconstruction quality (PSNR against the ground truth, K = 100) of the
+    1080p frame over the spatial weight decay rho and the damping gamma."""
+    truth = d_img.double()
+
+    def psnr(rho, gamma):
+        pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=rho, gamma=gamma)
+        fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        torch.cuda.synchronize()
+        mse = float(torch.mean((d_out.double() - truth) ** 2))
+        return 10 * np.log10(255.0 ** 2 / mse)
+    return {"rho": [{"rho": r, "gamma": GAMMA, "psnr_db": psnr(r, GAMMA)} for r in (0.5, 0.6, 0.7, 0.8, 0.9)],
+            "gamma": [{"rho": RHO, "gamma": g, "psnr_db": psnr(RHO, g)} for g in (0.25, 0.5, 0.75, 1.0)]}
+
+
 def _measure_batch(fsr, handle, dev, torch):
     """48 images of mixed size/mask/K in one graph-captured persistent launch."""
     from paper_2202_13926_gb300 import synth
@@ -501,6 +516,7 @@ def main():
 
     if world == 1 and not args.no_k_sweep:
         line["k_sweep"] = _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torch)
+        line["param_sweep"] = _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch)
     if world == 1 and not args.no_batch:
         line["batch"] = _measure_batch(fsr, handle, dev, torch)
     if world == 1 and args.serve_seconds > 0:

@@ -387,6 +387,22 @@ class Handle:
     def check_status(self, stream=None):
         fsr_check_status(self.ptr, stream)
 
+    def reconstruct_channels(self, img, mask, out=None, stream=None, **kw):
+        """Multi-channel image (C, H, W) with one mask (H, W) or one per
+        channel (C, H, W): the C planes are reconstructed independently (FSR
+        works on single-channel images) in one batch launch."""
+        import torch
+        if img.dim() != 3:
+            raise ValueError("img must be (C, H, W)")
+        C = img.shape[0]
+        masks = [mask] * C if mask.dim() == 2 else [mask[c] for c in range(C)]
+        if out is None:
+            out = torch.empty_like(img)
+        p = make_params(**kw)
+        fsr_reconstruct_batch(self.ptr, [image_desc(img[c], masks[c], out[c], p.iters) for c in range(C)], p,
+                              stream)
+        return out
+
 
 # ---- serving form ------------------------------------------------------------
 

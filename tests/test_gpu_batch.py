@@ -207,3 +207,19 @@ def test_mixed_batch_48_images_full_size(fsr_mod, handle):
     print(f"mixed batch: {got.size} sampled pixels, within 0.5 {frac:.5f}, dPSNR {dpsnr:.5f} dB")
     assert frac >= PA.FRAC_MIN, frac
     assert dpsnr <= PA.PSNR_TOL_DB, dpsnr
+
+
+def test_multichannel_frame_equals_per_channel_calls(fsr_mod, handle):
+    """A (3, H, W) frame in one batch launch equals three single-image calls."""
+    dev = torch.device("cuda:0")
+    H, W = 72, 112
+    planes = np.stack([synth.sinusoid_image(H, W, seed=60 + c) for c in range(3)])
+    mask = synth.iid_mask(H, W, seed=63, missing=0.5)
+    ti = torch.from_numpy(planes).to(dev)
+    tm = torch.from_numpy(mask).to(dev)
+    out = handle.reconstruct_channels(ti, tm, iters=40)
+    torch.cuda.synchronize()
+    for c in range(3):
+        one = handle.reconstruct(ti[c].contiguous(), tm, iters=40)
+        torch.cuda.synchronize()
+        assert torch.equal(out[c], one), c
