@@ -258,7 +258,8 @@ bool step(fsr_server* s) {
                     d[j].iters = r->K;
                     d[j].seq_out = nullptr;
                 }
-                const long long total = fsri::build_table(s->h, n, d.data(), &s->p, s->h_tables[slot]);
+                // (errors go to this thread's own record, not to the handle the caller uses)
+                const long long total = fsri::build_table(nullptr, n, d.data(), &s->p, s->h_tables[slot]);
                 cudaStream_t cs = s->s_comp[slot];
                 cudaError_t e = total < 0 ? cudaErrorInvalidValue : cudaSuccess;
                 for (Request* r : batch)
