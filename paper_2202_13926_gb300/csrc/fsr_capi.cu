@@ -74,9 +74,15 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 int check_method(fsr_handle* h, const fsr_params* p) {
     if (!p) return fail(h, FSR_ERR_INVALID_ARG, "params is NULL");
     if (p->block <= 0 || p->border < 0) return fail(h, FSR_ERR_INVALID_ARG, "block must be > 0 and border >= 0");
-    if (p->block + 2 * p->border != fsrk::S)
-        return fail(h, FSR_ERR_UNSUPPORTED, "support B + 2L = %d; this build implements S = 32", p->block + 2 * p->border);
+    const int S = p->block + 2 * p->border;
+    if (S != fsrk::S && !fsrk::small_supported(S, p->block))
+        return fail(h, FSR_ERR_UNSUPPORTED,
+                    "support B + 2L = %d with B = %d; this build implements S = 32 (B in {2, 4, 8, 16}), "
+                    "S = 16 (B in {2, 4, 8}) and S = 8 (B in {2, 4})",
+                    S, p->block);
     if (b_index(p->block) < 0) return fail(h, FSR_ERR_UNSUPPORTED, "block %d not in {2, 4, 8, 16}", p->block);
+    if (S != fsrk::S && p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
+        return fail(h, FSR_ERR_UNSUPPORTED, "supports smaller than 32 run FSR_FP32 or FSR_FP64_DEBUG");
     if (!(p->rho > 0.f && p->rho <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "rho must be in (0, 1]");
     if (!(p->gamma > 0.f && p->gamma <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "gamma must be in (0, 1]");
     if (p->freq_weight != 0 && p->freq_weight != 1) return fail(h, FSR_ERR_INVALID_ARG, "freq_weight must be 0 or 1");
@@ -196,9 +202,10 @@ int read_status(fsr_handle* h) {
                 st);
 }
 
-// FP32 single image: a one-image work table in one of the handle's table
-// slots (used in turn; a slot is reused once the launch that read it has
-// finished), then the batch kernel with the handle's FP32 schedule.
+// FP32 single image (and any image of a support smaller than 32): a
+// one-image work table in one of the handle's table slots (used in turn; a
+// slot is reused once the launch that read it has finished), then the batch
+// kernel with the handle's schedule.
 int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                         const fsr_params* p, float* out, cudaStream_t stream) {
     const int slot = (int)(h->single_next++ % fsr_handle::kSingleSlots);
@@ -220,12 +227,15 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
     if (total < 0) return FSR_ERR_CUDA;
     if ((e = cudaMemcpyAsync(dev, host, table_bytes(1), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
-    const fsrk::Schedule sc = h->sched[FSR_FP32][b_index(p->block)];
+    const fsrk::Schedule sc = h->sched[p->precision == FSR_FP64_DEBUG ? 1 : 0][b_index(p->block)];
     fsrk::BatchArgs a = batch_args(h, dev, 1, total, p, sc.chunk);
     a.empty = h->d_empty;
     a.tx_extra = h->inject_tile_fault ? 16 : 0;
     h->inject_tile_fault = 0;
-    if ((e = fsrk::launch_batch_fp32(a, p->block, sc, h->sm_count, stream)) != cudaSuccess)
+    const int S = p->block + 2 * p->border;
+    if (S != fsrk::S) e = fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, 1, h->sm_count, stream);
+    else e = fsrk::launch_batch_fp32(a, p->block, sc, h->sm_count, stream);
+    if (e != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     if ((e = cudaEventRecord(h->single_ev[slot], stream)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
@@ -235,7 +245,8 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
 
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                    const fsr_params* p, float* out, cudaStream_t stream) {
-    if (p->precision == FSR_FP32) return enqueue_single_fp32(h, img, mask, height, width, pitch, p, out, stream);
+    if (p->precision == FSR_FP32 || p->block + 2 * p->border != fsrk::S)
+        return enqueue_single_fp32(h, img, mask, height, width, pitch, p, out, stream);
     fsrk::KernelArgs a;
     std::memset(&a, 0, sizeof a);
     a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
@@ -299,7 +310,7 @@ long long build_table(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_p
     for (int j = 0; j < n; ++j) {
         const fsr_image_desc& x = d[order[j]];
         imgs[j] = image_args(x.img, x.mask, x.out, x.seq_out, x.height, x.width, x.pitch, x.iters, p->block);
-        if (tiles_possible(x.img, x.mask, x.pitch)) {
+        if (p->block + 2 * p->border == fsrk::S && tiles_possible(x.img, x.mask, x.pitch)) {
             fsrk::TileMaps tm;   // encoded at its own alignment, then copied into the table
             if (encode_tile_maps(h, x.img, x.mask, x.height, x.width, x.pitch, &tm) != FSR_OK) return -1;
             std::memcpy(maps + sizeof(fsrk::TileMaps) * (size_t)j, &tm, sizeof tm);
@@ -331,6 +342,9 @@ cudaError_t launch_batch(const fsrk::BatchArgs& a, const fsr_params* p, fsrk::Sc
                          cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    const int S = p->block + 2 * p->border;
+    if (S != fsrk::S)
+        return fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, sc.chunk, sm_count, s);
     return (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(a, p->block, sc, sm_count, s)
                                              : fsrk::launch_batch_fp32(a, p->block, sc, sm_count, s);
 }
@@ -449,7 +463,7 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
     if (!(prop.major == 10 && prop.minor == 3))
         return fail(nullptr, FSR_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only",
                     cfg->device, prop.major, prop.minor);
-    if ((e = fsrk::configure_fp32_batch()) != cudaSuccess ||
+    if ((e = fsrk::configure_fp32_batch()) != cudaSuccess || (e = fsrk::configure_small()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
         (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));

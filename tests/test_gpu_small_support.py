@@ -1,0 +1,124 @@
+"""Supports smaller than 32 (S = B + 2L in {8, 16}; the support-size study of
+Sec. IV): the small-support kernel against the FP64 oracle, which takes any S."""
+import numpy as np
+import pytest
+
+import oracle
+import parity as PA
+from paper_2202_13926_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [(16, 4), (16, 2), (16, 8), (8, 4), (8, 2)]   # (S, B)
+
+
+@pytest.fixture(scope="module")
+def fsr_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_13926_gb300 import fsr
+    return fsr
+
+
+@pytest.fixture(scope="module")
+def handle(fsr_mod):
+    h = fsr_mod.Handle(0)
+    yield h
+    h.close()
+
+
+def _run(handle, img, mask, S, B, K, precision="fp32", seq=False):
+    dev = torch.device("cuda:0")
+    n = -(-img.shape[0] // B) * -(-img.shape[1] // B)
+    seq_t = torch.full((n * max(K, 1),), -7, dtype=torch.int16, device=dev) if seq else None
+    out = handle.reconstruct(torch.from_numpy(np.ascontiguousarray(img)).to(dev),
+                             torch.from_numpy(np.ascontiguousarray(mask)).to(dev),
+                             block=B, border=(S - B) // 2, iters=K, precision=precision, seq_out=seq_t)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    if seq:
+        return o, seq_t.cpu().numpy().reshape(-1, max(K, 1))[:, :K]
+    return o
+
+
+def _oracle(img, mask, S, B, K):
+    r = oracle.fsr_image_blocks(img, mask, B=B, L=(S - B) // 2, K=K)
+    return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B), r
+
+
+@pytest.mark.parametrize("S,B", CASES)
+def test_fp32_matches_the_oracle(handle, S, B):
+    img, mask = synth.small_case()
+    got = _run(handle, img, mask, S, B, 100)
+    ref, _ = _oracle(img, mask, S, B, 100)
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    frac = PA.frac_within(got, ref)
+    assert frac >= PA.FRAC_MIN, (S, B, frac)
+    dpsnr = abs(PA.psnr(got, img) - PA.psnr(ref, img))
+    assert dpsnr <= PA.PSNR_TOL_DB, (S, B, dpsnr)
+
+
+@pytest.mark.parametrize("S,B", CASES)
+def test_fp64_selection_sequences(handle, S, B):
+    img, mask = synth.small_case(seed=4)
+    got, seq = _run(handle, img, mask, S, B, 60, precision="fp64", seq=True)
+    ref, r = _oracle(img, mask, S, B, 60)
+    n_hard, n_tie = PA.sequence_mismatches(seq, r["seq"], r["margin"])
+    assert n_hard == 0, (S, B, n_hard, n_tie)
+    assert np.max(np.abs(got - ref)) <= 1e-3
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (5, 7), (37, 53), (70, 9)])
+def test_ragged_sizes_and_edges(handle, H, W):
+    img = synth.sinusoid_image(H, W, seed=H * 7 + W)
+    mask = synth.iid_mask(H, W, seed=H + W, missing=0.6)
+    for S, B in ((16, 4), (8, 2)):
+        got, seq = _run(handle, img, mask, S, B, 20, precision="fp64", seq=True)
+        ref, r = _oracle(img, mask, S, B, 20)
+        assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+        n_hard, _ = PA.sequence_mismatches(seq, r["seq"], r["margin"])
+        assert n_hard == 0, (H, W, S, B)
+        assert np.max(np.abs(got - ref)) <= 1e-3
+
+
+def test_empty_supports_and_batch_form(fsr_mod, handle):
+    """Large holes leave 16 x 16 supports without known pixels (counted like
+    the oracle, output 0); the batch form equals the single-image form."""
+    fsr = fsr_mod
+    H, W = 96, 120
+    img = synth.sinusoid_image(H, W, seed=71)
+    m = synth.macroblock_mask(H, W, seed=72, lost=0.5, mb=32)
+    ref, r = _oracle(img, m, 16, 4, 30)
+    assert r["n_empty"] > 0
+    fsr.fsr_empty_blocks(handle.ptr)
+    single = _run(handle, img, m, 16, 4, 30)
+    assert fsr.fsr_empty_blocks(handle.ptr) == r["n_empty"]
+    assert PA.frac_within(single, ref) >= PA.FRAC_MIN
+    dev = torch.device("cuda:0")
+    items = []
+    for i, (hh, ww) in enumerate([(H, W), (40, 56)]):
+        im = img if i == 0 else synth.sinusoid_image(hh, ww, seed=73)
+        mk = m if i == 0 else synth.iid_mask(hh, ww, seed=74, missing=0.5)
+        ti, tm = torch.from_numpy(im).to(dev), torch.from_numpy(mk).to(dev)
+        items.append((im, mk, ti, tm, torch.full_like(ti, -1.0)))
+    p = fsr.make_params(block=4, border=6, iters=30)
+    fsr.fsr_reconstruct_batch(handle.ptr, [fsr.image_desc(ti, tm, to, 30) for _, _, ti, tm, to in items], p)
+    torch.cuda.synchronize()
+    for im, mk, ti, tm, to in items:
+        alone = _run(handle, im, mk, 16, 4, 30)
+        assert np.array_equal(to.cpu().numpy().astype(np.float64), alone)
+
+
+def test_unsupported_support_sizes_are_rejected(fsr_mod, handle):
+    fsr = fsr_mod
+    img, mask = synth.small_case()
+    dev = torch.device("cuda:0")
+    ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
+    for kw in (dict(block=4, border=10), dict(block=16, border=0), dict(block=4, border=6, precision="tc_tf32")):
+        with pytest.raises(fsr.FsrError) as e:
+            handle.reconstruct(ti, tm, **kw)
+        assert e.value.code == fsr.FSR_ERR_UNSUPPORTED, kw
