@@ -260,6 +260,31 @@ def _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torc
     return {"points": rows, "ms_per_iteration": per_iter, "prologue_ms": rows[0]["ms_per_frame"]}
 
 
+def _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
+    """Time per 1080p frame and PSNR for support sizes S = 8, 16, 32 (B = 4,
+    L = (S - B) / 2, K = 100; the support-size study of Sec. IV, Fig. 3)."""
+    truth = d_img.double()
+    rows = []
+    for S in (8, 16, 32):
+        pm = fsr.make_params(block=B, border=(S - B) // 2, iters=K_ITERS, rho=RHO, gamma=GAMMA)
+        for _ in range(2):
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        ts = []
+        for i in range(5):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        mse = float(torch.mean((d_out.double() - truth) ** 2))
+        ms = float(np.median(ts))
+        rows.append({"S": S, "ms_per_frame": ms, "fps": 1e3 / ms, "psnr_db": 10 * np.log10(255.0 ** 2 / mse)})
+    return rows
+
+
 def _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch):
     """Reconstruction quality (PSNR against the ground truth, K = 100) of the
     1080p frame over the spatial weight decay rho and the damping gamma."""
@@ -517,6 +542,7 @@ def main():
     if world == 1 and not args.no_k_sweep:
         line["k_sweep"] = _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torch)
         line["param_sweep"] = _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch)
+        line["s_sweep"] = _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
     if world == 1 and not args.no_batch:
         line["batch"] = _measure_batch(fsr, handle, dev, torch)
     if world == 1 and args.serve_seconds > 0:

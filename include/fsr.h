@@ -69,7 +69,9 @@ typedef struct fsr_config {
 /* Method parameters (Sec. II; defaults of Sec. IV: B=4, rho=0.7, gamma=0.5). */
 typedef struct fsr_params {
     int block;        /* B: target block size; one of 2, 4, 8, 16 */
-    int border;       /* L: border; S = B + 2L must equal 32 */
+    int border;       /* L: border; the support S = B + 2L is 32 (any B), 16 (B in
+                         {2, 4, 8}) or 8 (B in {2, 4}); S < 32 runs FSR_FP32 and
+                         FSR_FP64_DEBUG only */
     int iters;        /* K: number of iterations, 0 <= K <= 65535 */
     float rho;        /* rho-hat of Eq. (5), in (0, 1] */
     float gamma;      /* gamma of Eqs. (11)-(12), in (0, 1] */
@@ -107,7 +109,8 @@ const char *fsr_last_error(const fsr_handle *h);
  *   stream cudaStream_t (NULL = legacy default stream); the call only
  *          enqueues work and returns.
  * Errors: INVALID_ARG (NULL pointers, sizes <= 0, pitch < width, overlap,
- * parameters out of range), UNSUPPORTED (S != 32, block not in {2,4,8,16}),
+ * parameters out of range), UNSUPPORTED (a support or block size not listed at
+ * fsr_params.border, a tensor-core mode with S < 32),
  * CUDA (launch failure). */
 int fsr_reconstruct(fsr_handle *h, const float *img, const uint8_t *mask,
                     int height, int width, int pitch, const fsr_params *p,

@@ -226,10 +226,15 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
             }
             // a5: block maximum, lowest lane holding it, its first component
             T Mx = mx;
+            if constexpr (sizeof(T) == 4) {
+                // objective values are >= +0: their bit patterns order like the values
+                Mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(float(mx))));
+            } else {
 #pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                const T oth = __shfl_xor_sync(FULL, Mx, s);
-                Mx = oth > Mx ? oth : Mx;
+                for (int s = 16; s > 0; s >>= 1) {
+                    const T oth = __shfl_xor_sync(FULL, Mx, s);
+                    Mx = oth > Mx ? oth : Mx;
+                }
             }
             const int ul = __ffs(__ballot_sync(FULL, mx == Mx)) - 1;
             int pf = P - 1;
