@@ -426,14 +426,18 @@ template <typename T> struct WRow;
 template <> struct WRow<float> { static constexpr int stride = S + S / 2 + 2; };  // 48 entries + pad: 400 B
 template <> struct WRow<double> { static constexpr int stride = 2 * S + 1; };  // 1040 B
 
+// Row stride of the w_f table: one pad entry, so that 32 lanes reading
+// w_f[lane][l] hit 32 different banks.
+constexpr int WFS = S + 1;
+
 template <typename T>
 struct SmemLayout {
     using T2 = typename Vec2<T>::type;
     static constexpr int WS = WRow<T>::stride;
     // CTA-shared tables
     static constexpr size_t w0_off = 0;                                 // S*S T
-    static constexpr size_t wf_off = w0_off + sizeof(T) * S * S;        // S*S T
-    static constexpr size_t cs_off = wf_off + sizeof(T) * S * S;        // S T2
+    static constexpr size_t wf_off = w0_off + sizeof(T) * S * S;        // S*WFS T
+    static constexpr size_t cs_off = wf_off + sizeof(T) * S * WFS;      // S T2
     static constexpr size_t warp0_off = cs_off + sizeof(T2) * S;
     // per warp: W rows, then the published row
     static constexpr size_t w_elems = (size_t)S * WS;
@@ -852,7 +856,7 @@ __device__ __forceinline__ Pick argmax_pick(const float (&zr)[S], const float (&
         const float2 w = Wd[u * WS32 + cl];
         split_value(ar, ai, w.x, w.y, q.x, q.y, rr, ri);
     }
-    const float o = objective<float>(rr, ri, swf[u * S + cl]);
+    const float o = objective<float>(rr, ri, swf[u * WFS + cl]);
     const int vl = __ffs(__ballot_sync(FULL, __float_as_uint(o) == Mb)) - 1;   // lanes 0..GS-1 lead
     Pick pk;
     pk.u = u;
@@ -905,7 +909,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
     if (K <= 0) return;
     float wfr[S / 2 + 1];
 #pragma unroll
-    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
+    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * WFS + l];
     int pm[P], pn[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -959,7 +963,7 @@ __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double
     constexpr int WS = WRow<double>::stride;
     double wfr[S / 2 + 1];
 #pragma unroll
-    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * S + l];
+    for (int l = 0; l <= S / 2; ++l) wfr[l] = swf[lane * WFS + l];
     int pm[P], pn[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -987,7 +991,7 @@ __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double
         const double2 q = rowbuf[lane];
         double rr = q.x, ri = q.y;
         if (split) split_value(ar, ai, Wd[u * WS + lane].x, Wd[u * WS + lane].y, q.x, q.y, rr, ri);
-        const double o = objective<double>(rr, ri, swf[u * S + lane]);
+        const double o = objective<double>(rr, ri, swf[u * WFS + lane]);
         const int v = __ffs(__ballot_sync(FULL, o == M)) - 1;
         const double Rr = __shfl_sync(FULL, rr, v);
         const double Ri = __shfl_sync(FULL, ri, v);
@@ -1046,7 +1050,7 @@ __device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf
             const T b = T(1) - sqrt(T(2)) * r;
             wfv = b * b;
         }
-        swf[i] = wfv;
+        swf[m * WFS + n] = wfv;
     }
     for (int t = threadIdx.x; t < S; t += blockDim.x) {
         T2 v;
