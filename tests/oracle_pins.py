@@ -308,6 +308,55 @@ def pin_block_ignores_unknown_values(lib):
     assert np.array_equal(a["seq"], b["seq"]) and np.array_equal(a["g"], b["g"])
 
 
+def pin_small_supports(lib):
+    """The same facts at the support sizes of the support-size study (S = 8,
+    16): spatial-domain residual, exhaustive argmax, exact energy decrease,
+    exact recovery of a cosine and the tiling of an image with L = (S - 4) / 2."""
+    for S_ in (8, 16):
+        wf = lib.freq_weight(S_)
+        for seed, gamma in ((40 + S_, 0.5), (41 + S_, 0.8)):
+            f, known = _rand_block(seed, S=S_)
+            K = 12
+            res = lib.fsr_block(f, known, K=K, gamma=gamma, history=True)
+            G = _model_history(res, gamma, K, S=S_)
+            fw_tilde = np.where(known, f, 0.0)
+            w = res["w"]
+            W0 = w.sum()
+            scale = np.max(np.abs(res["R0"]))
+            E = [_energy(fw_tilde, w, G[nu]) for nu in range(K + 1)]
+            for nu in range(K):
+                Rb = np.fft.fft2((fw_tilde - np.fft.ifft2(G[nu])) * w)
+                assert np.max(np.abs(res["R_hist"][nu] - Rb)) <= 1e-10 * scale, (S_, seed, nu)
+                obj = wf * np.abs(res["R_hist"][nu]) ** 2
+                assert int(res["seq"][nu]) == int(np.argmax(obj)), (S_, seed, nu)
+                R = res["R_hist"][nu].flat[res["seq"][nu]]
+                want = (2 * gamma - gamma ** 2) * abs(R) ** 2 / W0
+                assert abs((E[nu] - E[nu + 1]) - want) <= 1e-9 * E[0], (S_, seed, nu)
+        m, n = np.mgrid[0:S_, 0:S_]
+        u, v = 1, S_ // 2 - 1
+        f = 20.0 * np.cos(2 * np.pi * (u * m + v * n) / S_ + 0.4)
+        res = lib.fsr_block(f, np.ones((S_, S_), bool), K=2, rho=1.0, gamma=1.0, freq_weight=False)
+        assert list(res["seq"]) == sorted([u * S_ + v, ((-u) % S_) * S_ + (-v) % S_])
+        assert np.max(np.abs(res["g"] - f)) <= 1e-10 * 20.0
+        # image tiling with B = 4, L = (S - 4) / 2
+        rng = np.random.default_rng(50 + S_)
+        H, Wd, B, L, K = 23, 29, 4, (S_ - 4) // 2, 8
+        img = rng.uniform(0, 255, (H, Wd)).astype(np.float32)
+        mask = (rng.random((H, Wd)) < 0.4).astype(np.uint8)
+        nbx, nby = -(-Wd // B), -(-H // B)
+        ids = np.array([0, nbx - 1, nbx * 2 + 3, nbx * nby - 1])
+        r = lib.fsr_image_blocks(img, mask, B=B, L=L, K=K, block_ids=ids, threads=1)
+        for s_, b in enumerate(ids):
+            f, kn, by, bx = _support(img, mask, int(b), B, L)
+            rb = lib.fsr_block(f, kn, K=K)
+            assert np.array_equal(r["seq"][s_], rb["seq"])
+            for a_ in range(B):
+                for c_ in range(B):
+                    y, x = by * B + a_, bx * B + c_
+                    if y < H and x < Wd and not mask[y, x]:
+                        assert abs(r["target"][s_, a_, c_] - rb["g"][L + a_, L + c_].real) <= 1e-9 * 255
+
+
 ALL_PINS = [
     pin_weights_closed_form,
     pin_weight_symmetries,
@@ -324,4 +373,5 @@ ALL_PINS = [
     pin_tiling_matches_block_routine,
     pin_image_edge_cases,
     pin_block_ignores_unknown_values,
+    pin_small_supports,
 ]
