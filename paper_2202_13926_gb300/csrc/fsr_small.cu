@@ -27,7 +27,11 @@ struct SmallLayout {
     using T2 = typename Vec2<T>::type;
     static constexpr int SS = SZ * SZ;
     static constexpr int P = SS / 32;              // components per lane
-    static constexpr int WROW = SZ + P;            // W row with its first P entries repeated
+    // Row strides with padding against bank conflicts: the lanes of a
+    // half-warp touch 8 (S = 16) or 4 (S = 8) different rows at once.
+    static constexpr int XS = SZ + 1;              // x, w of the support (T)
+    static constexpr int YS = SZ + 1;              // first-pass outputs (T2)
+    static constexpr int WROW = 2 * SZ + 1;        // W row: its S entries, the first P again, pad
     // CTA tables: w0, w_f (SS T each), e^{-j 2 pi t / S} (S T2)
     static constexpr size_t w0_off = 0;
     static constexpr size_t wf_off = w0_off + sizeof(T) * SS;
@@ -35,9 +39,9 @@ struct SmallLayout {
     static constexpr size_t warp0_off = (tw_off + sizeof(T2) * SZ + 127) & ~(size_t)127;
     // per warp: region A = x and w of the support (prologue), then the W rows;
     // region B = the first-pass outputs Yx, Yw
-    static constexpr size_t a_bytes = sizeof(T2) * SZ * WROW > 2 * sizeof(T) * SS ? sizeof(T2) * SZ * WROW
-                                                                                  : 2 * sizeof(T) * SS;
-    static constexpr size_t b_bytes = 2 * sizeof(T2) * SS;
+    static constexpr size_t a_bytes = sizeof(T2) * SZ * WROW > 2 * sizeof(T) * SZ * XS ? sizeof(T2) * SZ * WROW
+                                                                                       : 2 * sizeof(T) * SZ * XS;
+    static constexpr size_t b_bytes = 2 * sizeof(T2) * SZ * YS;
     static constexpr size_t per_warp = (a_bytes + b_bytes + 127) & ~(size_t)127;
     static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
 };
@@ -73,13 +77,13 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
                                             unsigned long long* empty, int lane) {
     using T2 = typename Vec2<T>::type;
     using Lay = SmallLayout<T, SZ>;
-    constexpr int SS = Lay::SS, P = Lay::P, WROW = Lay::WROW;
+    constexpr int P = Lay::P, WROW = Lay::WROW, XS = Lay::XS, YS = Lay::YS;
     constexpr int PT = TargetPix<B>::P;
     T* xs = reinterpret_cast<T*>(area);                 // region A (prologue)
-    T* ws = xs + SS;
+    T* ws = xs + SZ * XS;
     T2* Wr = reinterpret_cast<T2*>(area);               // region A (after pass 1)
     T2* Yx = reinterpret_cast<T2*>(area + Lay::a_bytes);
-    T2* Yw = Yx + SS;
+    T2* Yw = Yx + SZ * YS;
 
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -105,8 +109,8 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
         }
         const T f = kn ? T(fv) : T(0);   // select: unknown values never enter arithmetic
         const T w = kn ? sw0[i] : T(0);
-        xs[i] = f;
-        ws[i] = w;
+        xs[m * XS + n] = f;
+        ws[m * XS + n] = w;
         sw += w;
         sfw += w * f;
         anyk |= kn ? 1u : 0u;
@@ -125,7 +129,8 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
 #pragma unroll
         for (int j = 0; j < P; ++j) {
             const int i = lane + 32 * j;
-            xs[i] = ws[i] > T(0) ? (xs[i] - mu) * ws[i] : T(0);
+            const int x = (i / SZ) * XS + i % SZ;
+            xs[x] = ws[x] > T(0) ? (xs[x] - mu) * ws[x] : T(0);
         }
         __syncwarp();
 
@@ -134,8 +139,8 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
             T xr[SZ], wr_[SZ];
 #pragma unroll
             for (int n = 0; n < SZ; ++n) {
-                xr[n] = xs[k * SZ + n];
-                wr_[n] = ws[k * SZ + n];
+                xr[n] = xs[k * XS + n];
+                wr_[n] = ws[k * XS + n];
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -152,8 +157,8 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
                 T2 vx, vw;
                 vx.x = axr; vx.y = axi;
                 vw.x = awr; vw.y = awi;
-                Yx[k * SZ + l] = vx;   // row m = k of this lane
-                Yw[k * SZ + l] = vw;
+                Yx[k * YS + l] = vx;   // row m = k of this lane
+                Yw[k * YS + l] = vw;
             }
         }
         __syncwarp();
@@ -172,8 +177,8 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
                 const T2 t = stw[(k * m) & (SZ - 1)];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    const T2 a = Yx[m * SZ + l0 + p];
-                    const T2 b = Yw[m * SZ + l0 + p];
+                    const T2 a = Yx[m * YS + l0 + p];
+                    const T2 b = Yw[m * YS + l0 + p];
                     zr[p] = fma_rn(a.x, t.x, fma_rn(-a.y, t.y, zr[p]));
                     zi[p] = fma_rn(a.x, t.y, fma_rn(a.y, t.x, zi[p]));
                     wv[p].x = fma_rn(b.x, t.x, fma_rn(-b.y, t.y, wv[p].x));
