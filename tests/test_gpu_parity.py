@@ -203,3 +203,27 @@ def test_empty_blocks_are_counted_like_the_oracle(handle):
     to = torch.empty_like(ti)
     fsr.fsr_reconstruct_batch(handle.ptr, [fsr.image_desc(ti, tm, to, 10)], fsr.make_params(iters=10))
     assert fsr.fsr_empty_blocks(handle.ptr) == n_ref
+
+
+def test_many_calls_in_flight_on_two_streams(handle):
+    """Single-image calls take their work tables from a ring of handle slots:
+    150 calls queued on two streams without a synchronisation in between (more
+    than the ring holds) each give the result of a call made alone."""
+    from paper_2202_13926_gb300 import fsr
+    dev = torch.device("cuda:0")
+    imgs = [synth.sinusoid_image(48, 64, seed=80 + i) for i in range(5)]
+    masks = [synth.iid_mask(48, 64, seed=90 + i, missing=0.5) for i in range(5)]
+    ti = [torch.from_numpy(x).to(dev) for x in imgs]
+    tm = [torch.from_numpy(x).to(dev) for x in masks]
+    alone = []
+    for i in range(5):
+        alone.append(handle.reconstruct(ti[i], tm[i], iters=20))
+        torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.full_like(ti[0], -1.0) for _ in range(150)]
+    p = fsr.make_params(iters=20)
+    for j in range(150):
+        fsr.fsr_reconstruct(handle.ptr, ti[j % 5], tm[j % 5], p, outs[j], streams[j % 2])
+    torch.cuda.synchronize()
+    for j in range(150):
+        assert torch.equal(outs[j], alone[j % 5]), j
