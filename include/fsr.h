@@ -46,7 +46,7 @@ extern "C" {
 #define FSR_ERR_OOM         2   /* a device or pinned allocation failed / cap exceeded */
 #define FSR_ERR_CUDA        3   /* a CUDA runtime call or a kernel launch failed */
 #define FSR_ERR_TIMEOUT     4   /* a bounded device-side wait gave up */
-#define FSR_ERR_UNSUPPORTED 5   /* valid request this build does not implement */
+#define FSR_ERR_UNSUPPORTED 5   /* valid request this library does not implement */
 
 /* Arithmetic of the iteration (fsr_params.precision). */
 #define FSR_FP32       0  /* FP32 everywhere (the production path) */
@@ -84,7 +84,7 @@ typedef struct fsr_params {
 
 typedef struct fsr_handle fsr_handle;
 
-/* Create a handle on cfg->device.  Checks that the device runs this build
+/* Create a handle on cfg->device.  Checks that the device runs this library
  * (sm_103a) and sets the kernels' shared-memory limits.
  * Errors: INVALID_ARG (NULL pointers, bad ordinal), UNSUPPORTED (other GPU),
  * CUDA.  On error *out is set to NULL. */

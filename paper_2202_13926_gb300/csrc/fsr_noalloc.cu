@@ -68,7 +68,7 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
                       "split the batch or use fsr_reconstruct_batch",
                       n, kMaxImages, kScratchBytes);
     if (p->block + 2 * p->border != fsrk::S || !(p->block == 2 || p->block == 4 || p->block == 8 || p->block == 16))
-        return report(err, err_len, FSR_ERR_UNSUPPORTED, "block %d / border %d: this build implements S = 32, B in {2,4,8,16}",
+        return report(err, err_len, FSR_ERR_UNSUPPORTED, "block %d / border %d: the allocation-free entry point implements S = 32, B in {2,4,8,16}",
                       p->block, p->border);
     if (!(p->rho > 0.f && p->rho <= 1.f) || !(p->gamma > 0.f && p->gamma <= 1.f) ||
         (p->freq_weight != 0 && p->freq_weight != 1))
