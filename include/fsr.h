@@ -28,7 +28,10 @@
  * text of the last error of a handle is available from fsr_last_error().
  * Device pointers are owned by the caller; the library owns only its handle
  * and the workspace it allocates inside it.  Entry points that take a stream
- * are asynchronous on that stream unless stated otherwise.
+ * are asynchronous on that stream unless stated otherwise; work of one
+ * handle may be queued on several streams at once.  A handle is not
+ * thread-safe: calls on one handle must not overlap in time on the host (use
+ * one handle per host thread; a server's entry points are thread-safe).
  */
 #ifndef FSR_GB300_H
 #define FSR_GB300_H

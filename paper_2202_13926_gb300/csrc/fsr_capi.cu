@@ -235,11 +235,11 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
     const int S = p->block + 2 * p->border;
     if (S != fsrk::S) e = fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, 1, h->sm_count, stream);
     else e = fsrk::launch_batch_fp32(a, p->block, sc, h->sm_count, stream);
-    if (e != cudaSuccess)
-        return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-    if ((e = cudaEventRecord(h->single_ev[slot], stream)) != cudaSuccess)
-        return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
-    h->single_used[slot] = true;
+    // the slot is busy until the stream has passed this point (upload and launch)
+    const cudaError_t er = cudaEventRecord(h->single_ev[slot], stream);
+    if (er == cudaSuccess) h->single_used[slot] = true;
+    if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    if (er != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(er));
     return ok(h);
 }
 
