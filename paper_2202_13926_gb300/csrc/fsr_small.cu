@@ -208,28 +208,17 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
         }
         const T invW0 = T(1) / W0;
         T o[P];
-        T ar = mu, ai = T(0);
-        bool split = true;   // R = a W + Q until the first non-DC selection
         int nu = 0;
         T cr = T(0), ci = T(0);
         int u = 0, v = 0;
-        while (nu < im.K) {
-            // objective of every component (split or plain) and this lane's maximum
-            T rr[P], ri[P];
-            T mx = T(0);
+
+        // a5 for the objectives o[] of this lane's components with values
+        // (vr, vi): block maximum, lowest lane holding it, its first
+        // component; a6: c, the recorded index, the target pixels.
+        auto pick = [&](const T (&vr)[P], const T (&vi)[P]) {
+            T mx = o[0];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (split) {
-                    const T2 w = Wr[k * WROW + l0 + p];
-                    split_value(ar, ai, w.x, w.y, zr[p], zi[p], rr[p], ri[p]);
-                } else {
-                    rr[p] = zr[p];
-                    ri[p] = zi[p];
-                }
-                o[p] = objective<T>(rr[p], ri[p], wfv[p]);
-                mx = p == 0 ? o[p] : (o[p] > mx ? o[p] : mx);
-            }
-            // a5: block maximum, lowest lane holding it, its first component
+            for (int p = 1; p < P; ++p) mx = o[p] > mx ? o[p] : mx;
             T Mx = mx;
             if constexpr (sizeof(T) == 4) {
                 // objective values are >= +0: their bit patterns order like the values
@@ -243,22 +232,20 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
             }
             const int ul = __ffs(__ballot_sync(FULL, mx == Mx)) - 1;
             int pf = P - 1;
+            T sr = vr[P - 1], si = vi[P - 1];
 #pragma unroll
-            for (int p = P - 2; p >= 0; --p) pf = (o[p] == Mx) ? p : pf;
-            pf = __shfl_sync(FULL, pf, ul);
-            T sr = rr[0], si = ri[0];
-#pragma unroll
-            for (int p = 1; p < P; ++p) {
-                sr = (pf == p) ? rr[p] : sr;
-                si = (pf == p) ? ri[p] : si;
+            for (int p = P - 2; p >= 0; --p) {
+                const bool hit = o[p] == Mx;
+                pf = hit ? p : pf;
+                sr = hit ? vr[p] : sr;
+                si = hit ? vi[p] : si;
             }
+            pf = __shfl_sync(FULL, pf, ul);
             const T Rr = __shfl_sync(FULL, sr, ul);
             const T Ri = __shfl_sync(FULL, si, ul);
             const int c = ul * P + pf;
             u = c / SZ;
             v = c % SZ;
-
-            // a6
             cr = gamma * (Rr * invW0);
             ci = gamma * (Ri * invW0);
             if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * SZ + v);
@@ -267,29 +254,48 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
                 const T2 e = stw[(SZ - ((u * pm[q] + v * pn[q]) & (SZ - 1))) & (SZ - 1)];   // e^{+j...}
                 gacc[q] = fma_rn(cr, e.x, fma_rn(-ci, e.y, gacc[q]));   // Re(c e^{+j theta})
             }
-            ++nu;
-            if (nu == im.K) break;
+        };
 
-            // a7: DC bookkeeping or Eq. (12)
-            if (split) {
-                if ((u | v) == 0) {
-                    ar -= cr;
-                    ai -= ci;
-                    continue;
+        // ---- DC phase: R = a W + Q ----
+        bool done = im.K <= 0;
+        if (!done) {
+            T ar = mu, ai = T(0);
+            for (;;) {
+                T rr[P], ri[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const T2 w = Wr[k * WROW + l0 + p];
+                    split_value(ar, ai, w.x, w.y, zr[p], zi[p], rr[p], ri[p]);
+                    o[p] = objective<T>(rr[p], ri[p], wfv[p]);
                 }
+                pick(rr, ri);
+                if (++nu == im.K) {
+                    done = true;
+                    break;
+                }
+                if ((u | v) != 0) break;
+                ar -= cr;
+                ai -= ci;
+            }
+            if (!done) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const T2 w = Wr[k * WROW + l0 + p];
                     split_value(ar, ai, w.x, w.y, zr[p], zi[p], zr[p], zi[p]);
                 }
-                split = false;
             }
+        }
+        // ---- a7 (Eq. 12) for the last pick and the next objective, a5-a6 ----
+        while (!done) {
             const T2* row = Wr + ((k - u) & (SZ - 1)) * WROW + ((l0 - v) & (SZ - 1));
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const T2 w = row[p];
                 residual_update(zr[p], zi[p], w.x, w.y, cr, ci);
+                o[p] = objective<T>(zr[p], zi[p], wfv[p]);
             }
+            pick(zr, zi);
+            if (++nu == im.K) done = true;
         }
     } else if (lane == 0) {
         empty_block(seq, im.K, empty);
