@@ -281,7 +281,10 @@ def _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
             ts.append(a.elapsed_time(b))
         mse = float(torch.mean((d_out.double() - truth) ** 2))
         ms = float(np.median(ts))
-        rows.append({"S": S, "ms_per_frame": ms, "fps": 1e3 / ms, "psnr_db": 10 * np.log10(255.0 ** 2 / mse)})
+        nb = (-(-H // B)) * (-(-W // B))
+        smem = nb * K_ITERS * S * S * W_BYTES_PER_COMPONENT_ITER / (ms / 1e3) / 1e9
+        rows.append({"S": S, "ms_per_frame": ms, "fps": 1e3 / ms, "psnr_db": 10 * np.log10(255.0 ** 2 / mse),
+                     "smem_frac": smem / _smem_peak_gbs(torch, d_img.device)})
     return rows
 
 
@@ -298,6 +301,12 @@ def _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch):
         return 10 * np.log10(255.0 ** 2 / mse)
     return {"rho": [{"rho": r, "gamma": GAMMA, "psnr_db": psnr(r, GAMMA)} for r in (0.5, 0.6, 0.7, 0.8, 0.9)],
             "gamma": [{"rho": RHO, "gamma": g, "psnr_db": psnr(RHO, g)} for g in (0.25, 0.5, 0.75, 1.0)]}
+
+
+def _smem_peak_gbs(torch, dev):
+    """Derived shared-memory peak: SMs x 128 B/clk x maximum SM clock."""
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    return torch.cuda.get_device_properties(dev).multi_processor_count * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9
 
 
 def _measure_batch(fsr, handle, dev, torch):
@@ -336,6 +345,7 @@ def _measure_batch(fsr, handle, dev, torch):
                         "i.i.d. 10-90% or 16x16 macroblock 5-20% loss; K in {50,100,200}",
             "ms_per_batch": ms, "mp_per_s": mp / (ms / 1e3),
             "block_iterations_per_s": biters / (ms / 1e3),
+            "smem_frac": biters * 1024 * W_BYTES_PER_COMPONENT_ITER / (ms / 1e3) / 1e9 / _smem_peak_gbs(torch, dev),
             "schedule": {"warps": warps, "chunk": chunk, "tuned_on": "the 24 smaller images"},
             "graph": True}
 
