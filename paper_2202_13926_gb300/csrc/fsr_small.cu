@@ -216,9 +216,18 @@ __device__ __forceinline__ void small_block(const ImageArgs& im, long long blk, 
         // (vr, vi): block maximum, lowest lane holding it, its first
         // component; a6: c, the recorded index, the target pixels.
         auto pick = [&](const T (&vr)[P], const T (&vi)[P]) {
-            T mx = o[0];
+            T mx;
+            if constexpr (sizeof(T) == 4 && P == 8) {
+                mx = max3(max3(o[0], o[1], o[2]), max3(o[3], o[4], o[5]), fmaxf(o[6], o[7]));
+            } else if constexpr (sizeof(T) == 4) {
+                mx = o[0];
 #pragma unroll
-            for (int p = 1; p < P; ++p) mx = o[p] > mx ? o[p] : mx;
+                for (int p = 1; p < P; ++p) mx = fmaxf(mx, o[p]);
+            } else {
+                mx = o[0];
+#pragma unroll
+                for (int p = 1; p < P; ++p) mx = fmax(mx, o[p]);
+            }
             T Mx = mx;
             if constexpr (sizeof(T) == 4) {
                 // objective values are >= +0: their bit patterns order like the values
