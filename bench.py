@@ -39,6 +39,7 @@ PAPER_CONTEXT = {
     "seconds_per_1200x1200_image": 0.2276,
     "mp_per_s": 1.44 / 0.2276,
     "fhd_fps_at_S16": 8.86,
+    "fig3_seconds_per_image_by_S": {"4": 0.0593, "8": 0.0632, "16": 0.0804, "24": 0.1825, "32": 0.2276},
 }
 W_BYTES_PER_COMPONENT_ITER = 8       # complex FP32 W entry read per component per iteration
 FLOPS_PER_COMPONENT_ITER = 11        # objective 3 + complex multiply-subtract 8
@@ -261,11 +262,11 @@ def _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torc
 
 
 def _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
-    """Time per 1080p frame and PSNR for support sizes S = 8, 16, 32 (B = 4,
+    """Time per 1080p frame and PSNR for support sizes S = 8, 16, 24, 32 (B = 4,
     L = (S - B) / 2, K = 100; the support-size study of Sec. IV, Fig. 3)."""
     truth = d_img.double()
     rows = []
-    for S in (8, 16, 32):
+    for S in (8, 16, 24, 32):
         pm = fsr.make_params(block=B, border=(S - B) // 2, iters=K_ITERS, rho=RHO, gamma=GAMMA)
         for _ in range(2):
             fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)

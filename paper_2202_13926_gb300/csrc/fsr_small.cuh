@@ -1,0 +1,548 @@
+// FSR with a support S in {8, 16, 24} (Sec. II; the support-size study of
+// Sec. IV, Fig. 3): one warp per block.  Every lane holds a patch of RP rows
+// x CP columns of the spectrum (P = RP * CP = S*S/32 components; lane
+// a * (S/CP) + b holds rows a*RP .. a*RP+RP-1 and columns b*CP .. b*CP+CP-1),
+// in registers in row-major order.  For S = 8 and 16 a patch is one row
+// segment (RP = 1), so the linear index k*S + l of a lane's components grows
+// with the lane and with the register index; for S = 24 (RP = 3, CP = 6) the
+// lowest linear index among the maxima is found by a second warp reduction.
+//
+// The 2-D DFTs of the weighted signal and of the weights (Eq. 7) are two
+// direct separable passes through shared memory with a conjugate-symmetric
+// twiddle table and one summation order, which makes R_w and W exactly
+// Hermitian (the ties of the first iteration are exact, as in the oracle).
+// The iteration follows the S = 32 kernel: the weighted mean mu is removed
+// (R_w = mu W + Q), the DC phase keeps R = a W + Q, the objective of Eq. (8)
+// is rounded explicitly, the argmax takes the lowest linear index on ties,
+// the residual update of Eq. (12) reads W rows stored with their first
+// columns repeated (no column wrap), and Re g is accumulated at the B x B
+// target pixels only.  Work comes from the same work table and counter as
+// the S = 32 batch kernel.
+#pragma once
+
+#include "fsr_launch.h"
+
+namespace fsrk {
+namespace small {
+
+// cos(pi t / 12) for t = 0..6 (mathematical constants).
+__host__ __device__ constexpr double cos_pi12_base(int t) {
+    return t == 0 ? 1.0
+         : t == 1 ? 0.965925826289068286749743199728897367
+         : t == 2 ? 0.866025403784438646763723170752936183
+         : t == 3 ? 0.707106781186547524400844362104849039
+         : t == 4 ? 0.5
+         : t == 5 ? 0.258819045102520762348898837624048328
+         : 0.0;
+}
+// cos(2 pi t / 24) for any integer t, exact on the axes and at pi/3.
+__host__ __device__ constexpr double cos_2pi24(int t) {
+    t %= 24;
+    if (t < 0) t += 24;
+    return t <= 6 ? cos_pi12_base(t)
+         : t <= 12 ? -cos_pi12_base(12 - t)
+         : t <= 18 ? -cos_pi12_base(t - 12)
+         : cos_pi12_base(24 - t);
+}
+// cos and sin of 2 pi t / S for S in {8, 16, 24, 32}; cos(S - t) = cos(t) and
+// sin(S - t) = -sin(t) hold bit for bit.
+template <int SZ>
+__host__ __device__ constexpr double cos_2pi(int t) {
+    if constexpr (SZ == 24) return cos_2pi24(t);
+    else return cos_2pi32(t * (32 / SZ));
+}
+template <int SZ>
+__host__ __device__ constexpr double sin_2pi(int t) { return cos_2pi<SZ>(t - SZ / 4); }
+
+// The lane patch of a support size.
+template <int SZ> struct Shape;
+template <> struct Shape<8> { static constexpr int RP = 1, CP = 2; };
+template <> struct Shape<16> { static constexpr int RP = 1, CP = 8; };
+template <> struct Shape<24> { static constexpr int RP = 3, CP = 6; };
+
+template <int SZ>
+constexpr bool is_pow2() { return (SZ & (SZ - 1)) == 0; }
+
+template <typename T, int SZ>
+struct Layout {
+    using T2 = typename Vec2<T>::type;
+    static constexpr int SS = SZ * SZ;
+    static constexpr int RP = Shape<SZ>::RP, CP = Shape<SZ>::CP, P = RP * CP;
+    static_assert(P * 32 == SS, "the lane patches must tile the spectrum");
+    static_assert((SZ / CP) * (SZ / RP) == 32, "one patch per lane");
+    // Row strides with padding against bank conflicts: the lanes of a
+    // half-warp touch several rows at once.
+    static constexpr int XS = SZ + 1;              // x, w of the support (T)
+    static constexpr int YS = SZ + 1;              // first-pass outputs (T2)
+    static constexpr int WROW = 2 * SZ + 1;        // W row: its S entries, the first ones again, pad
+    // CTA tables: w0, w_f (SS T each), e^{-j 2 pi t / S} (S T2) and, when S is
+    // not a power of two, the products e^{-j 2 pi (a b mod S) / S} (SS T2).
+    static constexpr size_t w0_off = 0;
+    static constexpr size_t wf_off = w0_off + sizeof(T) * SS;
+    static constexpr size_t tw_off = wf_off + sizeof(T) * SS;
+    static constexpr size_t tt_off = tw_off + sizeof(T2) * SZ;
+    static constexpr size_t tt_bytes = is_pow2<SZ>() ? 0 : sizeof(T2) * SS;
+    static constexpr size_t warp0_off = (tt_off + tt_bytes + 127) & ~(size_t)127;
+    // Per warp: region A = x and w of the support (prologue); region B = the
+    // first-pass outputs Yx, Yw.  The W rows go to region A after the second
+    // pass when they fit there, else to region B (S = 24).
+    static constexpr size_t xw_bytes = 2 * sizeof(T) * SZ * XS;
+    static constexpr size_t w_bytes = sizeof(T2) * SZ * WROW;
+    static constexpr size_t b_bytes = 2 * sizeof(T2) * SZ * YS;
+    static constexpr bool W_IN_B = SZ == 24;
+    static_assert(!W_IN_B || w_bytes <= b_bytes, "W rows must fit in region B");
+    static constexpr size_t a_bytes = W_IN_B ? xw_bytes : (w_bytes > xw_bytes ? w_bytes : xw_bytes);
+    static constexpr size_t per_warp = (a_bytes + b_bytes + 127) & ~(size_t)127;
+    static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
+};
+
+// Warps per CTA: 8; FP64 at S = 24 takes 4 (shared memory per warp).
+template <typename T, int SZ>
+constexpr int warps() { return (sizeof(T) == 8 && SZ == 24) ? 4 : 8; }
+
+template <typename T, int SZ>
+__device__ __forceinline__ void tables(const MethodArgs& mth, T* sw0, T* swf, typename Vec2<T>::type* stw,
+                                       typename Vec2<T>::type* stt) {
+    const T half = T(SZ) / T(2);
+    for (int i = threadIdx.x; i < SZ * SZ; i += blockDim.x) {
+        const int m = i / SZ, n = i % SZ;
+        const T dm = T(m) - T(SZ - 1) / T(2), dn = T(n) - T(SZ - 1) / T(2);
+        sw0[i] = pow(T(mth.rho), sqrt(dm * dm + dn * dn));
+        T wfv = T(1);
+        if (mth.freq_weight) {
+            const T kt = half - fabs(T(m) - half), lt = half - fabs(T(n) - half);
+            const T r = sqrt(kt * kt / T(SZ * SZ) + lt * lt / T(SZ * SZ));
+            const T b = T(1) - sqrt(T(2)) * r;
+            wfv = b * b;
+        }
+        swf[i] = wfv;
+        if constexpr (!is_pow2<SZ>()) {
+            const int t = (m * n) % SZ;
+            typename Vec2<T>::type v;
+            v.x = T(cos_2pi<SZ>(t));
+            v.y = T(-sin_2pi<SZ>(t));
+            stt[i] = v;
+        }
+    }
+    for (int t = threadIdx.x; t < SZ; t += blockDim.x) {
+        typename Vec2<T>::type v;
+        v.x = T(cos_2pi<SZ>(t));
+        v.y = T(-sin_2pi<SZ>(t));   // e^{-j 2 pi t / S}
+        stw[t] = v;
+    }
+}
+
+// e^{-j 2 pi (a b mod S) / S}
+template <int SZ, typename T2>
+__device__ __forceinline__ T2 twiddle(const T2* stw, const T2* stt, int a, int b) {
+    if constexpr (is_pow2<SZ>()) return stw[(a * b) & (SZ - 1)];
+    else return stt[a * SZ + b];
+}
+
+// (i mod S) for i in (-S, S)
+template <int SZ>
+__device__ __forceinline__ int wrap(int i) {
+    if constexpr (is_pow2<SZ>()) return i & (SZ - 1);
+    else return i < 0 ? i + SZ : i;
+}
+
+// One block: a1-a9 for support size SZ, target B x B.
+template <typename T, int SZ, int B>
+__device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L, T gamma, const T* sw0,
+                                      const T* swf, const typename Vec2<T>::type* stw,
+                                      const typename Vec2<T>::type* stt, unsigned char* area,
+                                      unsigned long long* empty, int lane) {
+    using T2 = typename Vec2<T>::type;
+    using Lay = Layout<T, SZ>;
+    constexpr int P = Lay::P, RP = Lay::RP, CP = Lay::CP, WROW = Lay::WROW, XS = Lay::XS, YS = Lay::YS;
+    constexpr int PT = TargetPix<B>::P;
+    T* xs = reinterpret_cast<T*>(area);                 // region A (prologue)
+    T* ws = xs + SZ * XS;
+    T2* Yx = reinterpret_cast<T2*>(area + Lay::a_bytes);
+    T2* Yw = Yx + SZ * YS;
+    T2* Wr = Lay::W_IN_B ? Yx : reinterpret_cast<T2*>(area);   // after the second pass
+
+    const int by = (int)(blk / im.nbx);
+    const int bx = (int)(blk - (long long)by * im.nbx);
+    const int y0 = by * B - L, x0 = bx * B - L;
+    // this lane's patch: rows k0 .. k0+RP-1, columns l0 .. l0+CP-1
+    const int k0 = (lane / (SZ / CP)) * RP, l0 = (lane % (SZ / CP)) * CP;
+    int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
+
+    // ---- a1, a2: load the support, weights, weighted mean ----
+    __syncwarp();   // the area is free (previous block done)
+    T sw = T(0), sfw = T(0);
+    unsigned anyk = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int i = lane + 32 * j;
+        const int m = i / SZ, n = i % SZ;
+        const int y = y0 + m, x = x0 + n;
+        bool kn = false;
+        float fv = 0.f;
+        if ((unsigned)y < (unsigned)im.H && (unsigned)x < (unsigned)im.W) {
+            const size_t off = (size_t)y * im.pitch + x;
+            kn = __ldg(im.mask + off) != 0;
+            fv = __ldg(im.img + off);
+        }
+        const T f = kn ? T(fv) : T(0);   // select: unknown values never enter arithmetic
+        const T w = kn ? sw0[i] : T(0);
+        xs[m * XS + n] = f;
+        ws[m * XS + n] = w;
+        sw += w;
+        sfw += w * f;
+        anyk |= kn ? 1u : 0u;
+    }
+    T gacc[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) gacc[q] = T(0);
+
+    if (__ballot_sync(FULL, anyk != 0) != 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_xor_sync(FULL, sw, o);
+            sfw += __shfl_xor_sync(FULL, sfw, o);
+        }
+        const T mu = sfw / sw;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int i = lane + 32 * j;
+            const int x = (i / SZ) * XS + i % SZ;
+            xs[x] = ws[x] > T(0) ? (xs[x] - mu) * ws[x] : T(0);
+        }
+        __syncwarp();
+
+        // ---- a3, pass 1 (over n): Y[m][l] = sum_n v[m][n] e^{-j 2 pi l n / S},
+        //      for the rows m and columns l of this lane's patch ----
+        if constexpr (RP == 1) {
+            T xr[SZ], wr_[SZ];
+#pragma unroll
+            for (int n = 0; n < SZ; ++n) {
+                xr[n] = xs[k0 * XS + n];
+                wr_[n] = ws[k0 * XS + n];
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int l = l0 + p;
+                T axr = T(0), axi = T(0), awr = T(0), awi = T(0);
+#pragma unroll
+                for (int n = 0; n < SZ; ++n) {
+                    const T2 t = twiddle<SZ>(stw, stt, l, n);
+                    axr = fma_rn(xr[n], t.x, axr);
+                    axi = fma_rn(xr[n], t.y, axi);
+                    awr = fma_rn(wr_[n], t.x, awr);
+                    awi = fma_rn(wr_[n], t.y, awi);
+                }
+                T2 vx, vw;
+                vx.x = axr; vx.y = axi;
+                vw.x = awr; vw.y = awi;
+                Yx[k0 * YS + l] = vx;
+                Yw[k0 * YS + l] = vw;
+            }
+        } else {
+            T axr[P], axi[P], awr[P], awi[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) axr[p] = axi[p] = awr[p] = awi[p] = T(0);
+#pragma unroll 4
+            for (int n = 0; n < SZ; ++n) {
+                T2 t[CP];
+#pragma unroll
+                for (int j = 0; j < CP; ++j) t[j] = twiddle<SZ>(stw, stt, l0 + j, n);
+#pragma unroll
+                for (int r = 0; r < RP; ++r) {
+                    const T xv = xs[(k0 + r) * XS + n], wv = ws[(k0 + r) * XS + n];
+#pragma unroll
+                    for (int j = 0; j < CP; ++j) {
+                        const int p = r * CP + j;
+                        axr[p] = fma_rn(xv, t[j].x, axr[p]);
+                        axi[p] = fma_rn(xv, t[j].y, axi[p]);
+                        awr[p] = fma_rn(wv, t[j].x, awr[p]);
+                        awi[p] = fma_rn(wv, t[j].y, awi[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RP; ++r)
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    const int p = r * CP + j;
+                    T2 vx, vw;
+                    vx.x = axr[p]; vx.y = axi[p];
+                    vw.x = awr[p]; vw.y = awi[p];
+                    Yx[(k0 + r) * YS + l0 + j] = vx;
+                    Yw[(k0 + r) * YS + l0 + j] = vw;
+                }
+        }
+        __syncwarp();
+
+        // ---- a3, pass 2 (over m): Z[k][l] = sum_m Y[m][l] e^{-j 2 pi k m / S} ----
+        T zr[P], zi[P], w0r = T(0);
+        {
+            T2 wv[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                zr[p] = zi[p] = T(0);
+                wv[p].x = wv[p].y = T(0);
+            }
+#pragma unroll
+            for (int m = 0; m < SZ; ++m) {
+                T2 t[RP];
+#pragma unroll
+                for (int r = 0; r < RP; ++r) t[r] = twiddle<SZ>(stw, stt, k0 + r, m);
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    const T2 a = Yx[m * YS + l0 + j];
+                    const T2 b = Yw[m * YS + l0 + j];
+#pragma unroll
+                    for (int r = 0; r < RP; ++r) {
+                        const int p = r * CP + j;
+                        zr[p] = fma_rn(a.x, t[r].x, fma_rn(-a.y, t[r].y, zr[p]));
+                        zi[p] = fma_rn(a.x, t[r].y, fma_rn(a.y, t[r].x, zi[p]));
+                        wv[p].x = fma_rn(b.x, t[r].x, fma_rn(-b.y, t[r].y, wv[p].x));
+                        wv[p].y = fma_rn(b.x, t[r].y, fma_rn(b.y, t[r].x, wv[p].y));
+                    }
+                }
+            }
+            __syncwarp();   // the region the W rows go to is read no more
+#pragma unroll
+            for (int r = 0; r < RP; ++r)
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    const int p = r * CP + j;
+                    Wr[(k0 + r) * WROW + l0 + j] = wv[p];
+                    if (l0 + j < CP) Wr[(k0 + r) * WROW + SZ + l0 + j] = wv[p];
+                }
+            if (lane == 0) w0r = wv[0].x;   // W[0][0] (component 0 of lane 0)
+        }
+        const T W0 = __shfl_sync(FULL, w0r, 0);
+        __syncwarp();
+
+        // ---- a4-a8 ----
+        T wfv[P];
+#pragma unroll
+        for (int r = 0; r < RP; ++r)
+#pragma unroll
+            for (int j = 0; j < CP; ++j) wfv[r * CP + j] = swf[(k0 + r) * SZ + l0 + j];
+        int pm[PT], pn[PT];
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            pm[q] = L + (lane + 32 * q) / B;
+            pn[q] = L + (lane + 32 * q) % B;
+        }
+        const T invW0 = T(1) / W0;
+        T o[P];
+        int nu = 0;
+        T cr = T(0), ci = T(0);
+        int u = 0, v = 0;
+
+        // a5 for the objectives o[] of this lane's components with values
+        // (vr, vi): block maximum, then the lowest linear index holding it;
+        // a6: c, the recorded index, the target pixels.
+        auto pick = [&](const T (&vr)[P], const T (&vi)[P]) {
+            T mx;
+            if constexpr (sizeof(T) == 4 && P == 8) {
+                mx = max3(max3(o[0], o[1], o[2]), max3(o[3], o[4], o[5]), fmaxf(o[6], o[7]));
+            } else if constexpr (sizeof(T) == 4) {
+                mx = o[0];
+#pragma unroll
+                for (int p = 1; p + 1 < P; p += 2) mx = max3(mx, o[p], o[p + 1]);
+                if constexpr ((P - 1) % 2 != 0) mx = fmaxf(mx, o[P - 1]);
+            } else {
+                mx = o[0];
+#pragma unroll
+                for (int p = 1; p < P; ++p) mx = fmax(mx, o[p]);
+            }
+            T Mx = mx;
+            if constexpr (sizeof(T) == 4) {
+                // objective values are >= +0: their bit patterns order like the values
+                Mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(float(mx))));
+            } else {
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const T oth = __shfl_xor_sync(FULL, Mx, s);
+                    Mx = oth > Mx ? oth : Mx;
+                }
+            }
+            int c;
+            T sr = vr[P - 1], si = vi[P - 1];
+            if constexpr (RP == 1) {
+                // lanes and registers are in linear order: lowest lane, then lowest register
+                const int ul = __ffs(__ballot_sync(FULL, mx == Mx)) - 1;
+                int pf = P - 1;
+#pragma unroll
+                for (int p = P - 2; p >= 0; --p) {
+                    const bool hit = o[p] == Mx;
+                    pf = hit ? p : pf;
+                    sr = hit ? vr[p] : sr;
+                    si = hit ? vi[p] : si;
+                }
+                pf = __shfl_sync(FULL, pf, ul);
+                sr = __shfl_sync(FULL, sr, ul);
+                si = __shfl_sync(FULL, si, ul);
+                c = ul * P + pf;
+            } else {
+                // registers are in row-major order within the patch: the lane's
+                // first hit is its lowest linear index; the warp minimum of the
+                // lanes' candidates is the block's
+                unsigned cand = 0x7fff0000u;
+#pragma unroll
+                for (int p = P - 1; p >= 0; --p) {
+                    const bool hit = o[p] == Mx;
+                    cand = hit ? (unsigned)((p / CP) * SZ + p % CP) : cand;
+                    sr = hit ? vr[p] : sr;
+                    si = hit ? vi[p] : si;
+                }
+                cand += (unsigned)(k0 * SZ + l0);
+                unsigned cmin = __reduce_min_sync(FULL, cand);
+                const int ul = __ffs(__ballot_sync(FULL, cand == cmin)) - 1;
+                if (cmin >= (unsigned)(SZ * SZ)) cmin = 0;   // no lane matched (NaN objective): stay in range
+                sr = __shfl_sync(FULL, sr, ul);
+                si = __shfl_sync(FULL, si, ul);
+                c = (int)cmin;
+            }
+            u = c / SZ;
+            v = c % SZ;
+            cr = gamma * (sr * invW0);
+            ci = gamma * (si * invW0);
+            if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * SZ + v);
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                int ph;
+                if constexpr (is_pow2<SZ>()) ph = (SZ - ((u * pm[q] + v * pn[q]) & (SZ - 1))) & (SZ - 1);
+                else {
+                    ph = (u * pm[q] + v * pn[q]) % SZ;
+                    ph = ph == 0 ? 0 : SZ - ph;
+                }
+                const T2 e = stw[ph];   // e^{+j 2 pi (u m + v n) / S}
+                gacc[q] = fma_rn(cr, e.x, fma_rn(-ci, e.y, gacc[q]));   // Re(c e^{+j theta})
+            }
+        };
+
+        // ---- DC phase: R = a W + Q ----
+        bool done = im.K <= 0;
+        if (!done) {
+            T ar = mu, ai = T(0);
+            for (;;) {
+                T rr[P], ri[P];
+#pragma unroll
+                for (int r = 0; r < RP; ++r)
+#pragma unroll
+                    for (int j = 0; j < CP; ++j) {
+                        const int p = r * CP + j;
+                        const T2 w = Wr[(k0 + r) * WROW + l0 + j];
+                        split_value(ar, ai, w.x, w.y, zr[p], zi[p], rr[p], ri[p]);
+                        o[p] = objective<T>(rr[p], ri[p], wfv[p]);
+                    }
+                pick(rr, ri);
+                if (++nu == im.K) {
+                    done = true;
+                    break;
+                }
+                if ((u | v) != 0) break;
+                ar -= cr;
+                ai -= ci;
+            }
+            if (!done) {
+#pragma unroll
+                for (int r = 0; r < RP; ++r)
+#pragma unroll
+                    for (int j = 0; j < CP; ++j) {
+                        const int p = r * CP + j;
+                        const T2 w = Wr[(k0 + r) * WROW + l0 + j];
+                        split_value(ar, ai, w.x, w.y, zr[p], zi[p], zr[p], zi[p]);
+                    }
+            }
+        }
+        // ---- a7 (Eq. 12) for the last pick and the next objective, a5-a6 ----
+        while (!done) {
+            const int lc = wrap<SZ>(l0 - v);
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                const T2* row = Wr + wrap<SZ>(k0 + r - u) * WROW + lc;
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    const int p = r * CP + j;
+                    const T2 w = row[j];
+                    residual_update(zr[p], zi[p], w.x, w.y, cr, ci);
+                    o[p] = objective<T>(zr[p], zi[p], wfv[p]);
+                }
+            }
+            pick(zr, zi);
+            if (++nu == im.K) done = true;
+        }
+    } else if (lane == 0) {
+        empty_block(seq, im.K, empty);
+    }
+
+    // ---- a9: write-back of the B x B target ----
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int pidx = lane + 32 * q;
+        if (pidx < B * B) {
+            const int ty = by * B + pidx / B, tx = bx * B + pidx % B;
+            if (ty < im.H && tx < im.W) {
+                const size_t off = (size_t)ty * im.pitch + tx;
+                const bool kn = __ldg(im.mask + off) != 0;
+                im.out[off] = kn ? __ldg(im.img + off) : (float)gacc[q];
+            }
+        }
+    }
+}
+
+template <typename T, int SZ, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) fsr_small_kernel(const BatchArgs a) {
+    using Lay = Layout<T, SZ>;
+    using T2 = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
+    T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
+    T2* stw = reinterpret_cast<T2*>(smem + Lay::tw_off);
+    T2* stt = reinterpret_cast<T2*>(smem + Lay::tt_off);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* area = smem + Lay::warp0_off + Lay::per_warp * warp;
+    tables<T, SZ>(a.mth, sw0, swf, stw, stt);
+    __syncthreads();
+
+    const T gamma = T(a.mth.gamma);
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= (unsigned long long)a.total) break;
+        const long long end = min((long long)base + a.chunk, a.total);
+        for (long long item = (long long)base; item < end; ++item) {
+            int lo = 0, hi = a.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.first + mid) <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            const ImageArgs im = a.images[lo];
+            block<T, SZ, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, stw, stt, area, a.empty,
+                            lane);
+        }
+    }
+}
+
+template <typename T, int SZ, int B>
+cudaError_t configure_one() {
+    constexpr int W = warps<T, SZ>();
+    return cudaFuncSetAttribute(fsr_small_kernel<T, SZ, B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Layout<T, SZ>::bytes(W));
+}
+
+template <typename T, int SZ, int B>
+cudaError_t launch_one(const BatchArgs& a, int chunk, int sm_count, cudaStream_t stream) {
+    constexpr int W = warps<T, SZ>();
+    const size_t smem = Layout<T, SZ>::bytes(W);
+    int grid = 0;
+    cudaError_t e = persistent_grid(fsr_small_kernel<T, SZ, B, W>, W, smem, (a.total + chunk - 1) / chunk,
+                                    sm_count, &grid);
+    if (e != cudaSuccess) return e;
+    fsr_small_kernel<T, SZ, B, W><<<grid, W * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace small
+}  // namespace fsrk

@@ -77,7 +77,7 @@ def pin_weights_closed_form(lib):
 
 
 def pin_weight_symmetries(lib):
-    for S_ in (8, 16, 32):
+    for S_ in (8, 16, 24, 32):
         w = lib.spatial_weight(S_, 0.7)
         # symmetric about the support centre in both axes and under transposition
         assert np.array_equal(w, w[::-1, :]) and np.array_equal(w, w[:, ::-1])
@@ -95,7 +95,7 @@ def pin_weight_symmetries(lib):
 
 def pin_dft_against_numpy(lib):
     rng = np.random.default_rng(5)
-    for S_ in (8, 16, 32):
+    for S_ in (8, 16, 24, 32):
         x = rng.standard_normal((S_, S_)) * 50 + 10
         X = lib.dft2_real(x)
         ref = np.fft.fft2(x)
@@ -310,10 +310,15 @@ def pin_block_ignores_unknown_values(lib):
 
 def pin_small_supports(lib):
     """The same facts at the support sizes of the support-size study (S = 8,
-    16): spatial-domain residual, exhaustive argmax, exact energy decrease,
+    16, 24): spatial-domain residual, exhaustive argmax, exact energy decrease,
     exact recovery of a cosine and the tiling of an image with L = (S - 4) / 2."""
-    for S_ in (8, 16):
+    for S_ in (8, 16, 24):
         wf = lib.freq_weight(S_)
+        # exactly Hermitian spectra at every support size (the ties of nu = 0 are exact)
+        r0 = lib.fsr_block(*_rand_block(60 + S_, S=S_), K=1)
+        n_ = _neg(S_)
+        for X in (r0["R0"], r0["W"]):
+            assert np.array_equal(X, np.conj(X[n_][:, n_])), S_
         for seed, gamma in ((40 + S_, 0.5), (41 + S_, 0.8)):
             f, known = _rand_block(seed, S=S_)
             K = 12

@@ -155,7 +155,7 @@ def test_invalid_arguments_report_codes(handle):
     img, mask = synth.small_case()
     dev = torch.device("cuda:0")
     ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
-    cases = [dict(block=4, border=10), dict(block=6, border=13), dict(iters=-1),
+    cases = [dict(block=4, border=12), dict(block=6, border=13), dict(iters=-1),
              dict(rho=0.0), dict(gamma=1.5), dict(precision=7)]
     codes = [fsr.FSR_ERR_UNSUPPORTED, fsr.FSR_ERR_UNSUPPORTED, fsr.FSR_ERR_INVALID_ARG,
              fsr.FSR_ERR_INVALID_ARG, fsr.FSR_ERR_INVALID_ARG, fsr.FSR_ERR_UNSUPPORTED]

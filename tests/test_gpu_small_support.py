@@ -1,5 +1,5 @@
-"""Supports smaller than 32 (S = B + 2L in {8, 16}; the support-size study of
-Sec. IV): the small-support kernel against the FP64 oracle, which takes any S."""
+"""Supports smaller than 32 (S = B + 2L in {8, 16, 24}; the support-size study
+of Sec. IV): the small-support kernel against the FP64 oracle, which takes any S."""
 import numpy as np
 import pytest
 
@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CASES = [(16, 4), (16, 2), (16, 8), (8, 4), (8, 2)]   # (S, B)
+CASES = [(24, 4), (24, 8), (16, 4), (16, 2), (16, 8), (8, 4), (8, 2)]   # (S, B)
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +76,7 @@ def test_fp64_selection_sequences(handle, S, B):
 def test_ragged_sizes_and_edges(handle, H, W):
     img = synth.sinusoid_image(H, W, seed=H * 7 + W)
     mask = synth.iid_mask(H, W, seed=H + W, missing=0.6)
-    for S, B in ((16, 4), (8, 2)):
+    for S, B in ((24, 4), (16, 4), (8, 2)):
         got, seq = _run(handle, img, mask, S, B, 20, precision="fp64", seq=True)
         ref, r = _oracle(img, mask, S, B, 20)
         assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
@@ -118,7 +118,8 @@ def test_unsupported_support_sizes_are_rejected(fsr_mod, handle):
     img, mask = synth.small_case()
     dev = torch.device("cuda:0")
     ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
-    for kw in (dict(block=4, border=10), dict(block=16, border=0), dict(block=4, border=6, precision="tc_tf32")):
+    for kw in (dict(block=4, border=8), dict(block=2, border=11), dict(block=16, border=0),
+               dict(block=4, border=6, precision="tc_tf32")):
         with pytest.raises(fsr.FsrError) as e:
             handle.reconstruct(ti, tm, **kw)
         assert e.value.code == fsr.FSR_ERR_UNSUPPORTED, kw
