@@ -4,8 +4,12 @@
 // a * (S/CP) + b holds rows a*RP .. a*RP+RP-1 and columns b*CP .. b*CP+CP-1),
 // in registers in row-major order.  For S = 8 and 16 a patch is one row
 // segment (RP = 1), so the linear index k*S + l of a lane's components grows
-// with the lane and with the register index; for S = 24 (RP = 3, CP = 6) the
+// with the lane and with the register index; for S = 24 (RP = 6, CP = 3) the
 // lowest linear index among the maxima is found by a second warp reduction.
+// The 6 x 3 patches with W rows of 28 entries make the shifted W reads of
+// Eq. (12) free of bank conflicts for every (u, v): the eight column starts
+// 3b - v of a half-warp are distinct mod 8 and its two row groups are 6 rows
+// = 8 banks apart.
 //
 // The 2-D DFTs of the weighted signal and of the weights (Eq. 7) are two
 // direct separable passes through shared memory with a conjugate-symmetric
@@ -58,7 +62,7 @@ __host__ __device__ constexpr double sin_2pi(int t) { return cos_2pi<SZ>(t - SZ 
 template <int SZ> struct Shape;
 template <> struct Shape<8> { static constexpr int RP = 1, CP = 2; };
 template <> struct Shape<16> { static constexpr int RP = 1, CP = 8; };
-template <> struct Shape<24> { static constexpr int RP = 3, CP = 6; };
+template <> struct Shape<24> { static constexpr int RP = 6, CP = 3; };
 
 template <int SZ>
 constexpr bool is_pow2() { return (SZ & (SZ - 1)) == 0; }
@@ -72,33 +76,45 @@ struct Layout {
     static_assert((SZ / CP) * (SZ / RP) == 32, "one patch per lane");
     // Row strides with padding against bank conflicts: the lanes of a
     // half-warp touch several rows at once.
-    static constexpr int XS = SZ + 1;              // x, w of the support (T)
-    static constexpr int YS = SZ + 1;              // first-pass outputs (T2)
-    static constexpr int WROW = 2 * SZ + 1;        // W row: its S entries, the first ones again, pad
+    static constexpr int XS = SZ + 1;                      // x, w of the support (T)
+    static constexpr int YS = SZ == 24 ? 28 : SZ + 1;      // first-pass outputs (T2)
+    static constexpr int WROW = SZ == 24 ? 28 : 2 * SZ + 1;   // W row: its S entries, the first CP again, pad
+    static_assert(WROW >= SZ + CP - 1, "a shifted patch row is read without wrapping");
+    // W rows stored twice (rows S .. 2S-1 repeat 0 .. S-1) where RP > 1, so
+    // the RP rows of a shifted patch are read without a row wrap.
+    static constexpr int WROWS = RP > 1 ? 2 * SZ : SZ;
+    static constexpr int TTS = SZ + 1;                     // row stride of the twiddle products
     // CTA tables: w0, w_f (SS T each), e^{-j 2 pi t / S} (S T2) and, when S is
-    // not a power of two, the products e^{-j 2 pi (a b mod S) / S} (SS T2).
+    // not a power of two, the products e^{-j 2 pi (a b mod S) / S} (S x TTS T2).
     static constexpr size_t w0_off = 0;
     static constexpr size_t wf_off = w0_off + sizeof(T) * SS;
     static constexpr size_t tw_off = wf_off + sizeof(T) * SS;
     static constexpr size_t tt_off = tw_off + sizeof(T2) * SZ;
-    static constexpr size_t tt_bytes = is_pow2<SZ>() ? 0 : sizeof(T2) * SS;
+    static constexpr size_t tt_bytes = is_pow2<SZ>() ? 0 : sizeof(T2) * SZ * TTS;
     static constexpr size_t warp0_off = (tt_off + tt_bytes + 127) & ~(size_t)127;
-    // Per warp: region A = x and w of the support (prologue); region B = the
-    // first-pass outputs Yx, Yw.  The W rows go to region A after the second
-    // pass when they fit there, else to region B (S = 24).
+    // Per warp, S = 8, 16: region A = x and w of the support (prologue), then
+    // the W rows; region B = the first-pass outputs Yx, Yw.  S = 24 (IN_PLACE):
+    // one region that holds x and w, then (both passes accumulate in
+    // registers) Yx and Yw, then the W rows.
     static constexpr size_t xw_bytes = 2 * sizeof(T) * SZ * XS;
-    static constexpr size_t w_bytes = sizeof(T2) * SZ * WROW;
-    static constexpr size_t b_bytes = 2 * sizeof(T2) * SZ * YS;
-    static constexpr bool W_IN_B = SZ == 24;
-    static_assert(!W_IN_B || w_bytes <= b_bytes, "W rows must fit in region B");
-    static constexpr size_t a_bytes = W_IN_B ? xw_bytes : (w_bytes > xw_bytes ? w_bytes : xw_bytes);
-    static constexpr size_t per_warp = (a_bytes + b_bytes + 127) & ~(size_t)127;
+    static constexpr size_t w_bytes = sizeof(T2) * WROWS * WROW;
+    static constexpr size_t y_bytes = 2 * sizeof(T2) * SZ * YS;
+    static constexpr bool IN_PLACE = SZ == 24;
+    static constexpr size_t a_bytes = w_bytes > xw_bytes ? w_bytes : xw_bytes;
+    static constexpr size_t region = IN_PLACE ? (a_bytes > y_bytes ? a_bytes : y_bytes) : a_bytes + y_bytes;
+    // RP > 1: P entries where the lane holding the block maximum publishes its values
+    static constexpr size_t pub_off = (region + 15) & ~(size_t)15;
+    static constexpr size_t pub_bytes = RP > 1 ? sizeof(T2) * P : 0;
+    static constexpr size_t per_warp = (pub_off + pub_bytes + 127) & ~(size_t)127;
     static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
 };
 
-// Warps per CTA: 8; FP64 at S = 24 takes 4 (shared memory per warp).
+// Warps per CTA: 8; FP64 at S = 24 takes 4 (shared memory per warp).  FP32
+// at S = 24 runs two CTAs per SM (at most 128 registers).
 template <typename T, int SZ>
 constexpr int warps() { return (sizeof(T) == 8 && SZ == 24) ? 4 : 8; }
+template <typename T, int SZ>
+constexpr int min_ctas() { return (sizeof(T) == 4 && SZ == 24) ? 2 : 1; }
 
 template <typename T, int SZ>
 __device__ __forceinline__ void tables(const MethodArgs& mth, T* sw0, T* swf, typename Vec2<T>::type* stw,
@@ -121,7 +137,7 @@ __device__ __forceinline__ void tables(const MethodArgs& mth, T* sw0, T* swf, ty
             typename Vec2<T>::type v;
             v.x = T(cos_2pi<SZ>(t));
             v.y = T(-sin_2pi<SZ>(t));
-            stt[i] = v;
+            stt[m * Layout<T, SZ>::TTS + n] = v;
         }
     }
     for (int t = threadIdx.x; t < SZ; t += blockDim.x) {
@@ -136,7 +152,7 @@ __device__ __forceinline__ void tables(const MethodArgs& mth, T* sw0, T* swf, ty
 template <int SZ, typename T2>
 __device__ __forceinline__ T2 twiddle(const T2* stw, const T2* stt, int a, int b) {
     if constexpr (is_pow2<SZ>()) return stw[(a * b) & (SZ - 1)];
-    else return stt[a * SZ + b];
+    else return stt[a * (SZ + 1) + b];
 }
 
 // (i mod S) for i in (-S, S)
@@ -156,11 +172,12 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
     using Lay = Layout<T, SZ>;
     constexpr int P = Lay::P, RP = Lay::RP, CP = Lay::CP, WROW = Lay::WROW, XS = Lay::XS, YS = Lay::YS;
     constexpr int PT = TargetPix<B>::P;
-    T* xs = reinterpret_cast<T*>(area);                 // region A (prologue)
+    T* xs = reinterpret_cast<T*>(area);                 // prologue
     T* ws = xs + SZ * XS;
-    T2* Yx = reinterpret_cast<T2*>(area + Lay::a_bytes);
+    T2* Yx = reinterpret_cast<T2*>(Lay::IN_PLACE ? area : area + Lay::a_bytes);
     T2* Yw = Yx + SZ * YS;
-    T2* Wr = Lay::W_IN_B ? Yx : reinterpret_cast<T2*>(area);   // after the second pass
+    T2* Wr = reinterpret_cast<T2*>(area);               // after the second pass
+    T2* pub = reinterpret_cast<T2*>(area + Lay::pub_off);
 
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -243,7 +260,7 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
             T axr[P], axi[P], awr[P], awi[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) axr[p] = axi[p] = awr[p] = awi[p] = T(0);
-#pragma unroll 4
+#pragma unroll 1
             for (int n = 0; n < SZ; ++n) {
                 T2 t[CP];
 #pragma unroll
@@ -261,6 +278,7 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                     }
                 }
             }
+            if constexpr (Lay::IN_PLACE) __syncwarp();   // x, w are read no more: Y goes there
 #pragma unroll
             for (int r = 0; r < RP; ++r)
 #pragma unroll
@@ -311,6 +329,10 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                     const int p = r * CP + j;
                     Wr[(k0 + r) * WROW + l0 + j] = wv[p];
                     if (l0 + j < CP) Wr[(k0 + r) * WROW + SZ + l0 + j] = wv[p];
+                    if constexpr (Lay::WROWS > SZ) {
+                        Wr[(SZ + k0 + r) * WROW + l0 + j] = wv[p];
+                        if (l0 + j < CP) Wr[(SZ + k0 + r) * WROW + SZ + l0 + j] = wv[p];
+                    }
                 }
             if (lane == 0) w0r = wv[0].x;   // W[0][0] (component 0 of lane 0)
         }
@@ -334,12 +356,16 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         int nu = 0;
         T cr = T(0), ci = T(0);
         int u = 0, v = 0;
+        T ar = mu, ai = T(0);   // DC phase: R = a W + Q
+
+        T sr, si;   // the picked component's value
 
         // a5 for the objectives o[] of this lane's components with values
         // (vr, vi): block maximum, then the lowest linear index holding it;
-        // a6: c, the recorded index, the target pixels.
-        auto pick = [&](const T (&vr)[P], const T (&vi)[P]) {
-            T mx;
+        // sets u, v and (sr, si).
+        T mx, Mx;
+        // block maximum of the objectives o[]: this lane's (mx) and the warp's (Mx)
+        auto block_max = [&]() {
             if constexpr (sizeof(T) == 4 && P == 8) {
                 mx = max3(max3(o[0], o[1], o[2]), max3(o[3], o[4], o[5]), fmaxf(o[6], o[7]));
             } else if constexpr (sizeof(T) == 4) {
@@ -352,7 +378,7 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
 #pragma unroll
                 for (int p = 1; p < P; ++p) mx = fmax(mx, o[p]);
             }
-            T Mx = mx;
+            Mx = mx;
             if constexpr (sizeof(T) == 4) {
                 // objective values are >= +0: their bit patterns order like the values
                 Mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(float(mx))));
@@ -363,8 +389,13 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                     Mx = oth > Mx ? oth : Mx;
                 }
             }
+        };
+        // a5 after block_max: the lowest linear index holding Mx among this
+        // lane's components with values (vr, vi); sets u, v and (sr, si).
+        auto pick = [&](const T (&vr)[P], const T (&vi)[P]) {
             int c;
-            T sr = vr[P - 1], si = vi[P - 1];
+            sr = vr[P - 1];
+            si = vi[P - 1];
             if constexpr (RP == 1) {
                 // lanes and registers are in linear order: lowest lane, then lowest register
                 const int ul = __ffs(__ballot_sync(FULL, mx == Mx)) - 1;
@@ -402,6 +433,13 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
             }
             u = c / SZ;
             v = c % SZ;
+        };
+        auto select = [&](const T (&vr)[P], const T (&vi)[P]) {
+            block_max();
+            pick(vr, vi);
+        };
+        // a6 for the picked component: c, the recorded index, the target pixels.
+        auto apply = [&]() {
             cr = gamma * (sr * invW0);
             ci = gamma * (si * invW0);
             if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * SZ + v);
@@ -421,19 +459,37 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         // ---- DC phase: R = a W + Q ----
         bool done = im.K <= 0;
         if (!done) {
-            T ar = mu, ai = T(0);
             for (;;) {
-                T rr[P], ri[P];
+                if constexpr (RP == 1) {
+                    T rr[P], ri[P];
 #pragma unroll
-                for (int r = 0; r < RP; ++r)
-#pragma unroll
-                    for (int j = 0; j < CP; ++j) {
-                        const int p = r * CP + j;
-                        const T2 w = Wr[(k0 + r) * WROW + l0 + j];
+                    for (int p = 0; p < P; ++p) {
+                        const T2 w = Wr[k0 * WROW + l0 + p];
                         split_value(ar, ai, w.x, w.y, zr[p], zi[p], rr[p], ri[p]);
                         o[p] = objective<T>(rr[p], ri[p], wfv[p]);
                     }
-                pick(rr, ri);
+                    select(rr, ri);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RP; ++r)
+#pragma unroll
+                        for (int j = 0; j < CP; ++j) {
+                            const int p = r * CP + j;
+                            const T2 w = Wr[(k0 + r) * WROW + l0 + j];
+                            T rr_, ri_;
+                            split_value(ar, ai, w.x, w.y, zr[p], zi[p], rr_, ri_);
+                            o[p] = objective<T>(rr_, ri_, wfv[p]);
+                        }
+                    // the scan held Q: form the picked value a W[u][v] + Q[u][v]
+                    // with the same rounded operations
+                    select(zr, zi);
+                    const T2 w = Wr[u * WROW + v];
+                    T rr_, ri_;
+                    split_value(ar, ai, w.x, w.y, sr, si, rr_, ri_);
+                    sr = rr_;
+                    si = ri_;
+                }
+                apply();
                 if (++nu == im.K) {
                     done = true;
                     break;
@@ -456,9 +512,11 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         // ---- a7 (Eq. 12) for the last pick and the next objective, a5-a6 ----
         while (!done) {
             const int lc = wrap<SZ>(l0 - v);
+            // rows k0 - u + r (mod S): one base for the doubled rows
+            const T2* base = Wr + (RP > 1 ? k0 - u + SZ : 0) * WROW + lc;
 #pragma unroll
             for (int r = 0; r < RP; ++r) {
-                const T2* row = Wr + wrap<SZ>(k0 + r - u) * WROW + lc;
+                const T2* row = RP > 1 ? base + r * WROW : Wr + wrap<SZ>(k0 + r - u) * WROW + lc;
 #pragma unroll
                 for (int j = 0; j < CP; ++j) {
                     const int p = r * CP + j;
@@ -467,7 +525,47 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                     o[p] = objective<T>(zr[p], zi[p], wfv[p]);
                 }
             }
-            pick(zr, zi);
+            if constexpr (RP == 1) {
+                select(zr, zi);
+            } else {
+                block_max();
+                const unsigned cands = __ballot_sync(FULL, mx == Mx);
+                if (__popc(cands) == 1) {
+                    // One lane holds the block maximum: it publishes its values,
+                    // and lane t < P forms the objective of that lane's component
+                    // t again (the same rounded operations and w_f entry), so the
+                    // first lane that meets Mx has the lowest linear index.
+                    const int ul = __ffs(cands) - 1;
+                    __syncwarp();   // the previous pick's reads of pub are done
+                    if (lane == ul) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            T2 e;
+                            e.x = zr[p];
+                            e.y = zi[p];
+                            pub[p] = e;
+                        }
+                    }
+                    __syncwarp();
+                    const int kw = (ul / (SZ / CP)) * RP, lw = (ul % (SZ / CP)) * CP;
+                    T2 rv;
+                    rv.x = rv.y = T(0);
+                    bool hit = false;
+                    if (lane < P) {
+                        rv = pub[lane];
+                        hit = objective<T>(rv.x, rv.y, swf[(kw + lane / CP) * SZ + lw + lane % CP]) == Mx;
+                    }
+                    int pf = __ffs(__ballot_sync(FULL, hit)) - 1;
+                    if (pf < 0) pf = 0;   // unreachable: the lane's maximum is one of its objectives
+                    sr = __shfl_sync(FULL, rv.x, pf);
+                    si = __shfl_sync(FULL, rv.y, pf);
+                    u = kw + pf / CP;
+                    v = lw + pf % CP;
+                } else {
+                    pick(zr, zi);   // ties across lanes, or no lane matched
+                }
+            }
+            apply();
             if (++nu == im.K) done = true;
         }
     } else if (lane == 0) {
@@ -489,8 +587,8 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
     }
 }
 
-template <typename T, int SZ, int B, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) fsr_small_kernel(const BatchArgs a) {
+template <typename T, int SZ, int B>
+__device__ __forceinline__ void run(const BatchArgs& a) {
     using Lay = Layout<T, SZ>;
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -525,22 +623,38 @@ __global__ void __launch_bounds__(WARPS * 32) fsr_small_kernel(const BatchArgs a
     }
 }
 
+// One CTA per SM at most by launch bounds (the register count is the
+// compiler's), and the two-CTA form (at most 128 registers) for FP32 S = 24.
+template <typename T, int SZ, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) fsr_small_kernel(const BatchArgs a) {
+    run<T, SZ, B>(a);
+}
+template <typename T, int SZ, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2) fsr_small_kernel_2cta(const BatchArgs a) {
+    run<T, SZ, B>(a);
+}
+
+template <typename T, int SZ, int B>
+constexpr auto kernel_of() {
+    if constexpr (min_ctas<T, SZ>() == 2) return fsr_small_kernel_2cta<T, SZ, B, warps<T, SZ>()>;
+    else return fsr_small_kernel<T, SZ, B, warps<T, SZ>()>;
+}
+
 template <typename T, int SZ, int B>
 cudaError_t configure_one() {
-    constexpr int W = warps<T, SZ>();
-    return cudaFuncSetAttribute(fsr_small_kernel<T, SZ, B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Layout<T, SZ>::bytes(W));
+    return cudaFuncSetAttribute(kernel_of<T, SZ, B>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Layout<T, SZ>::bytes(warps<T, SZ>()));
 }
 
 template <typename T, int SZ, int B>
 cudaError_t launch_one(const BatchArgs& a, int chunk, int sm_count, cudaStream_t stream) {
     constexpr int W = warps<T, SZ>();
     const size_t smem = Layout<T, SZ>::bytes(W);
+    auto k = kernel_of<T, SZ, B>();
     int grid = 0;
-    cudaError_t e = persistent_grid(fsr_small_kernel<T, SZ, B, W>, W, smem, (a.total + chunk - 1) / chunk,
-                                    sm_count, &grid);
+    cudaError_t e = persistent_grid(k, W, smem, (a.total + chunk - 1) / chunk, sm_count, &grid);
     if (e != cudaSuccess) return e;
-    fsr_small_kernel<T, SZ, B, W><<<grid, W * 32, smem, stream>>>(a);
+    k<<<grid, W * 32, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
