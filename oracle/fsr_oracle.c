@@ -183,6 +183,70 @@ int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
             if (o && o->Rhim) memcpy(o->Rhim + (size_t)(nu + 1) * SS, Rim, sizeof(double) * SS);
             continue;
         }
+        if (P->conj_pairs) {
+            /* Ablation, not the paper's Eqs. (11)-(12): the real-valued model
+             * of the original FSR.  The basis pair phi_uv + its conjugate
+             * phi_{-u,-v} is added with the coefficients a = gamma p and a*
+             * (p of Eq. 10), so G stays Hermitian and g real:
+             *   G[u,v] += a S^2,  G[-u,-v] += a* S^2,
+             *   R_w[k,l] -= a W[k-u, l-v] + a* W[k+u, l+v]
+             * (the residual update of Eq. 12 applied to both basis images).
+             * A self-conjugate (u,v) (2u = 2v = 0 mod S) is one real basis
+             * image and takes the single update.  R_w stays Hermitian, so the
+             * members of a pair tie: the scan visits the member with the
+             * lower linear index only, which also keeps the margin meaningful.
+             * The sums and differences of the two W entries make the update of
+             * (-k,-l) the exact conjugate of that of (k,l). */
+            double top = -1.0, runner = -1.0;
+            int sel = 0;
+            for (int k = 0; k < S; ++k)
+                for (int l = 0; l < S; ++l) {
+                    const int lin = k * S + l, lin_conj = ((S - k) % S) * S + (S - l) % S;
+                    if (lin_conj < lin) continue;
+                    const double ob = wf[lin] * (Rre[lin] * Rre[lin] + Rim[lin] * Rim[lin]);
+                    if (ob > top) {
+                        runner = top;
+                        top = ob;
+                        sel = lin;
+                    } else if (ob > runner) {
+                        runner = ob;
+                    }
+                }
+            const int su = sel / S, sv = sel % S;
+            const int sel_conj = ((S - su) % S) * S + (S - sv) % S;
+            const double qre = Rre[sel] / W0, qim = Rim[sel] / W0;      /* Eq. (10) */
+            const double cre = P->gamma * qre, cim = P->gamma * qim;    /* a = gamma p */
+            Gre[sel] += cre * (double)SS;
+            Gim[sel] += cim * (double)SS;
+            if (sel_conj != sel) {
+                Gre[sel_conj] += cre * (double)SS;
+                Gim[sel_conj] -= cim * (double)SS;
+            }
+            for (int k = 0; k < S; ++k)
+                for (int l = 0; l < S; ++l) {
+                    const int d1 = ((k + S - su) % S) * S + (l + S - sv) % S;   /* W[k-u, l-v] */
+                    const int d2 = ((k + su) % S) * S + (l + sv) % S;           /* W[k+u, l+v] */
+                    double ur, ui;
+                    if (sel_conj == sel) {
+                        ur = cre * Wre[d1] - cim * Wim[d1];
+                        ui = cre * Wim[d1] + cim * Wre[d1];
+                    } else {
+                        const double sr = Wre[d1] + Wre[d2], si = Wim[d1] + Wim[d2];
+                        const double dr = Wre[d1] - Wre[d2], di = Wim[d1] - Wim[d2];
+                        ur = cre * sr - cim * di;    /* Re(a W1 + a* W2) */
+                        ui = cre * si + cim * dr;    /* Im(a W1 + a* W2) */
+                    }
+                    Rre[k * S + l] -= ur;
+                    Rim[k * S + l] -= ui;
+                }
+            if (o && o->seq) o->seq[nu] = sel;
+            if (o && o->pre) o->pre[nu] = qre;
+            if (o && o->pim) o->pim[nu] = qim;
+            if (o && o->margin) o->margin[nu] = top > 0.0 ? (top - runner) / top : 0.0;
+            if (o && o->Rhre) memcpy(o->Rhre + (size_t)(nu + 1) * SS, Rre, sizeof(double) * SS);
+            if (o && o->Rhim) memcpy(o->Rhim + (size_t)(nu + 1) * SS, Rim, sizeof(double) * SS);
+            continue;
+        }
         /* Eq. (8): exhaustive scan; strict '>' keeps the lowest index on ties. */
         double best = -1.0, second = -1.0;
         int idx = 0;

@@ -29,6 +29,9 @@ typedef struct {
     double rho;       /* spatial decay factor rho-hat, Eq. (5) */
     double gamma;     /* orthogonality deficiency compensation, Eqs. (11)-(12) */
     int freq_weight;  /* 1: objective w_f |R_w|^2 (Eq. 8); 0: |R_w|^2 */
+    int conj_pairs;   /* 0: the paper's single complex component per iteration
+                         (Eqs. 11-12); 1: ablation, the selected component and
+                         its conjugate together (a real model, see the .c file) */
 } fsr_oracle_params;
 
 /* Optional per-block outputs; any pointer may be NULL. */

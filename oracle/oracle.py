@@ -7,6 +7,9 @@ Each wrapper names the part of the paper its C routine follows:
   dft2_real       the 2-D DFT F2 of Eq. (7)
   fsr_block       Sec. II, Eqs. (2), (5)-(12) on one support block
   fsr_image_blocks Sec. III-A tiling, Eq. (13), plus the write-back of Sec. II
+With ``conj_pairs`` the two block routines run the ablation of the original
+FSR's real model (the selected component and its conjugate updated together),
+which is not the paper's Eqs. (11)-(12).
 """
 from __future__ import annotations
 
@@ -42,7 +45,8 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("S", ctypes.c_int), ("K", ctypes.c_int), ("rho", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("freq_weight", ctypes.c_int)]
+                ("gamma", ctypes.c_double), ("freq_weight", ctypes.c_int),
+                ("conj_pairs", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -109,7 +113,7 @@ class OracleLib:
 
     def fsr_block(self, f: np.ndarray, known: np.ndarray, K: int, rho: float = 0.7,
                   gamma: float = 0.5, freq_weight: bool = True,
-                  history: bool = False) -> dict:
+                  history: bool = False, conj_pairs: bool = False) -> dict:
         """FSR of one S x S support block (Sec. II).
 
         Returns w, R0, W, seq (u*S+v per iteration, -1 if skipped), p, margin,
@@ -120,7 +124,7 @@ class OracleLib:
         known = np.ascontiguousarray(known, np.uint8)
         S = f.shape[0]
         assert f.shape == (S, S) and known.shape == (S, S)
-        P = _Params(S, K, rho, gamma, int(bool(freq_weight)))
+        P = _Params(S, K, rho, gamma, int(bool(freq_weight)), int(bool(conj_pairs)))
         arrs = {n: np.empty((S, S)) for n in ("w", "R0re", "R0im", "Wre", "Wim",
                                                 "Gre", "Gim", "gre", "gim")}
         seq = np.empty(max(K, 1), np.int32)
@@ -151,7 +155,7 @@ class OracleLib:
     def fsr_image_blocks(self, img: np.ndarray, mask: np.ndarray, B: int = 4, L: int = 14,
                          K: int = 100, rho: float = 0.7, gamma: float = 0.5,
                          freq_weight: bool = True, block_ids=None,
-                         threads: int = 0) -> dict:
+                         threads: int = 0, conj_pairs: bool = False) -> dict:
         """FSR of selected target blocks of an image (Sec. III-A tiling).
 
         Returns ``target`` (n, B, B) float64 (NaN outside the image), ``seq``
@@ -174,7 +178,7 @@ class OracleLib:
         im_target = np.empty((n, B, B))
         seq = np.empty((n, max(K, 1)), np.int32)
         margin = np.empty((n, max(K, 1)))
-        P = _Params(B + 2 * L, K, rho, gamma, int(bool(freq_weight)))
+        P = _Params(B + 2 * L, K, rho, gamma, int(bool(freq_weight)), int(bool(conj_pairs)))
         r = self.lib.fsr_oracle_image_blocks(
             img.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, Wd, Wd, B, L,

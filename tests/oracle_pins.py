@@ -40,6 +40,24 @@ def _model_history(res, gamma, K, S=S):
     return G
 
 
+def _conj_model_history(res, gamma, K, S=S):
+    """G^(nu) of the conjugate-pair ablation: a = gamma p at the selected index
+    and conj(a) at its conjugate index (once for a self-conjugate index)."""
+    G = np.zeros((K + 1, S, S), complex)
+    n = _neg(S)
+    for nu in range(K):
+        G[nu + 1] = G[nu]
+        idx = int(res["seq"][nu])
+        if idx < 0:
+            continue
+        u, v = divmod(idx, S)
+        a = gamma * res["p"][nu] * S * S
+        G[nu + 1][u, v] += a
+        if (n[u], n[v]) != (u, v):
+            G[nu + 1][n[u], n[v]] += np.conj(a)
+    return G
+
+
 def _energy(fw_tilde, w, G):
     """Weighted residual energy of Eqs. (3)-(4) in the spatial domain for a
     model spectrum G (g = complex inverse DFT by numpy)."""
@@ -362,6 +380,58 @@ def pin_small_supports(lib):
                         assert abs(r["target"][s_, a_, c_] - rb["g"][L + a_, L + c_].real) <= 1e-9 * 255
 
 
+def pin_conj_pairs(lib):
+    """The conjugate-pair ablation (the original FSR's real model; not the
+    paper's Eqs. 11-12): the residual stays exactly Hermitian, equals the
+    spatial-domain residual of the real model, the selection is the first
+    maximum of the full scan, and each step lowers E_w by the closed form of
+    a real pair update with a = gamma R/W0:
+    2(2g - g^2)|R|^2/W0 - 2 g^2 Re(conj(R)^2 W[2u,2v])/W0^2, or
+    (2g - g^2) R^2/W0 for a self-conjugate (u,v)."""
+    for seed, gamma, S_ in ((70, 0.5, S), (71, 0.8, S), (72, 0.5, 16), (73, 0.5, 24)):
+        f, known = _rand_block(seed, S=S_)
+        K = 14
+        res = lib.fsr_block(f, known, K=K, gamma=gamma, history=True, conj_pairs=True)
+        n = _neg(S_)
+        wf = lib.freq_weight(S_)
+        fw_tilde = np.where(known, f, 0.0)
+        w = res["w"]
+        W0 = w.sum()
+        Wsp = res["W"]
+        G = _conj_model_history(res, gamma, K, S=S_)
+        scale = np.max(np.abs(res["R0"]))
+        E = [_energy(fw_tilde, w, G[nu]) for nu in range(K + 1)]
+        selfconj = 0
+        for nu in range(K):
+            R = res["R_hist"][nu]
+            assert np.array_equal(R, np.conj(R[n][:, n])), (S_, seed, nu)
+            Rb = np.fft.fft2((fw_tilde - np.fft.ifft2(G[nu]).real) * w)
+            assert np.max(np.abs(R - Rb)) <= 1e-10 * scale, (S_, seed, nu)
+            obj = wf * np.abs(R) ** 2
+            idx = int(res["seq"][nu])
+            assert idx == int(np.argmax(obj)), (S_, seed, nu)
+            u, v = divmod(idx, S_)
+            Ru = R.flat[idx]
+            if (n[u], n[v]) == (u, v):
+                selfconj += 1
+                want = (2 * gamma - gamma ** 2) * abs(Ru) ** 2 / W0
+            else:
+                want = (2 * (2 * gamma - gamma ** 2) * abs(Ru) ** 2 / W0
+                        - 2 * gamma ** 2 * (np.conj(Ru) ** 2 * Wsp[(2 * u) % S_, (2 * v) % S_]).real / W0 ** 2)
+            assert abs((E[nu] - E[nu + 1]) - want) <= 1e-9 * E[0], (S_, seed, nu)
+        assert selfconj > 0 and selfconj < K   # both kinds of update were exercised
+        assert np.max(np.abs(res["G"] - G[K])) <= 1e-9 * np.max(np.abs(G[K]))
+        assert np.max(np.abs(res["g"] - np.fft.ifft2(G[K]))) <= 1e-9 * 255
+        assert np.max(np.abs(res["g"].imag)) <= 1e-9 * 255
+    # a real cosine, every pixel known, rho = gamma = 1: one pair recovers it
+    m, n_ = np.mgrid[0:S, 0:S]
+    u, v = 3, 5
+    f = 20.0 * np.cos(2 * np.pi * (u * m + v * n_) / S + 0.4)
+    res = lib.fsr_block(f, np.ones((S, S), bool), K=1, rho=1.0, gamma=1.0, freq_weight=False, conj_pairs=True)
+    assert list(res["seq"]) == [min(u * S + v, ((-u) % S) * S + (-v) % S)]
+    assert np.max(np.abs(res["g"] - f)) <= 1e-10 * 20.0
+
+
 ALL_PINS = [
     pin_weights_closed_form,
     pin_weight_symmetries,
@@ -379,4 +449,5 @@ ALL_PINS = [
     pin_image_edge_cases,
     pin_block_ignores_unknown_values,
     pin_small_supports,
+    pin_conj_pairs,
 ]

@@ -45,6 +45,12 @@ MUTANTS = {
                       "if (o->gre) o->gre[m * S + n] = sr;"),
     "unknown_read": ("x[i] = known[i] ? f[i] * w[i] : 0.0;", "x[i] = f[i] * w[i];"),
     "weight_everywhere": ("w[i] = known[i] ? w0[i] : 0.0;", "w[i] = w0[i];"),
+    # the conjugate-pair ablation
+    "pair_model_not_conjugate": ("Gim[sel_conj] -= cim * (double)SS;", "Gim[sel_conj] += cim * (double)SS;"),
+    "pair_second_shift_sign": ("const int d2 = ((k + su) % S) * S + (l + sv) % S;",
+                               "const int d2 = ((k + S - su) % S) * S + (l + sv) % S;"),
+    "pair_update_diff_sign": ("ur = cre * sr - cim * di;", "ur = cre * sr + cim * di;"),
+    "pair_selfconj_doubled": ("if (sel_conj == sel) {", "if (0) {"),
 }
 
 
