@@ -289,6 +289,31 @@ def _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
     return rows
 
 
+def _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
+    """The conjugate-pair ablation (the original FSR's real model) against the
+    paper's single-component update on the 1080p frame, K = 100: time per
+    frame and PSNR."""
+    truth = d_img.double()
+    rows = {}
+    for upd in ("single", "conj_pair"):
+        pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, update=upd)
+        for _ in range(2):
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        ts = []
+        for i in range(5):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        mse = float(torch.mean((d_out.double() - truth) ** 2))
+        rows[upd] = {"ms_per_frame": float(np.median(ts)), "psnr_db": 10 * np.log10(255.0 ** 2 / mse)}
+    return rows
+
+
 def _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch):
     """Reconstruction quality (PSNR against the ground truth, K = 100) of the
     1080p frame over the spatial weight decay rho and the damping gamma."""
@@ -554,6 +579,7 @@ def main():
         line["k_sweep"] = _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torch)
         line["param_sweep"] = _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch)
         line["s_sweep"] = _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
+        line["ablation_update"] = _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
     if world == 1 and not args.no_batch:
         line["batch"] = _measure_batch(fsr, handle, dev, torch)
     if world == 1 and args.serve_seconds > 0:

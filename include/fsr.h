@@ -61,6 +61,15 @@ extern "C" {
 #define FSR_TC_BF16X3  2  /* operands split into BF16 hi + lo, products hi.hi + hi.lo + lo.hi */
 #define FSR_TC_TF32    3  /* operands rounded to TF32 */
 
+/* Model update per iteration (fsr_params.update). */
+#define FSR_UPDATE_SINGLE    0  /* the paper's: one complex component (Eqs. 11-12) */
+/* Ablation (the original FSR's real model; S = 32, B = 4, FSR_FP32 or
+ * FSR_FP64_DEBUG): with a = gamma p (Eq. 10) the selected component and its
+ * conjugate are updated together, G[u,v] += a S^2, G[-u,-v] += a* S^2,
+ * R_w[k,l] -= a W[k-u,l-v] + a* W[k+u,l+v] (once for a self-conjugate
+ * (u,v)), so R_w stays Hermitian and g real. */
+#define FSR_UPDATE_CONJ_PAIR 1
+
 /* Library configuration (fsr_create). */
 typedef struct fsr_config {
     int device;                  /* CUDA device ordinal the handle is bound to */
@@ -83,6 +92,7 @@ typedef struct fsr_params {
     int16_t *seq_out; /* optional DEVICE buffer of N*K entries (N = number of blocks,
                          block b = by*ceil(width/B) + bx): the selected u*S+v of each
                          iteration, -1 for a block without known pixels; NULL = off */
+    int update;       /* FSR_UPDATE_SINGLE (0, zero-initialised default) or FSR_UPDATE_CONJ_PAIR */
 } fsr_params;
 
 typedef struct fsr_handle fsr_handle;

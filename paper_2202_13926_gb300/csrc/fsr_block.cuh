@@ -792,6 +792,61 @@ __device__ __forceinline__ void pass_update(float (&zr)[S], float (&zi)[S], cons
     half_update<ODD>(zr, zi, wfr, row + ((s + S / 2) & (S - 1)), 1, cr, ci, g);
 }
 
+// Conjugate-pair ablation (the original FSR's real model): R -= c W1 + c* W2
+// with W1 = W[k-u][l-v], W2 = W[k+u][l+v], formed from the sum and the
+// difference of the two entries so that the update of (-k,-l) is the exact
+// conjugate of that of (k,l) (R stays exactly Hermitian).
+__device__ __forceinline__ void pair_update(float& re, float& im, float w1r, float w1i, float w2r, float w2i,
+                                            float cr, float ci) {
+    const float sr = w1r + w2r, si = w1i + w2i;
+    const float dr = w1r - w2r, di = w1i - w2i;
+    re = fma_rn(-cr, sr, fma_rn(ci, di, re));
+    im = fma_rn(-cr, si, fma_rn(-ci, dr, im));
+}
+
+template <bool ODD>
+__device__ __forceinline__ void half_update_pair(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
+                                                 const float2* base1, const float2* base2, int h, float cr,
+                                                 float ci, float (&g)[NG]) {
+    const float4* p1 = reinterpret_cast<const float4*>(ODD ? base1 - 1 : base1);
+    const float4* p2 = reinterpret_cast<const float4*>(ODD ? base2 - 1 : base2);
+    float4 prev1 = ODD ? p1[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 prev2 = ODD ? p2[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < S / 4; ++j) {
+        const int i = 8 * h + j;
+        float4 a, b;   // (entry 2i, entry 2i+1) of each row
+        if (ODD) {
+            const float4 n1 = p1[j + 1], n2 = p2[j + 1];
+            a = make_float4(prev1.z, prev1.w, n1.x, n1.y);
+            b = make_float4(prev2.z, prev2.w, n2.x, n2.y);
+            prev1 = n1;
+            prev2 = n2;
+        } else {
+            a = p1[j];
+            b = p2[j];
+        }
+        pair_update(zr[2 * i], zi[2 * i], a.x, a.y, b.x, b.y, cr, ci);
+        pair_update(zr[2 * i + 1], zi[2 * i + 1], a.z, a.w, b.z, b.w, cr, ci);
+        group_max(g, i, objective<float>(zr[2 * i], zi[2 * i], wf_at(wfr, 2 * i)),
+                  objective<float>(zr[2 * i + 1], zi[2 * i + 1], wf_at(wfr, 2 * i + 1)));
+    }
+}
+
+// Row k reads row1 = W[k-u] from column s1 = -v and row2 = W[k+u] from
+// column s2 = v (mod 32); s1 and s2 have the parity of v.
+template <bool ODD>
+__device__ __forceinline__ void pass_update_pair(float (&zr)[S], float (&zi)[S], const float (&wfr)[S / 2 + 1],
+                                                 const float2* row1, int s1, const float2* row2, int s2,
+                                                 float cr, float ci, float (&g)[NG]) {
+    half_update_pair<ODD>(zr, zi, wfr, row1 + s1, row2 + s2, 0, cr, ci, g);
+    half_update_pair<ODD>(zr, zi, wfr, row1 + ((s1 + S / 2) & (S - 1)), row2 + ((s2 + S / 2) & (S - 1)), 1, cr,
+                          ci, g);
+}
+
+// (u, v) is its own conjugate: 2u = 2v = 0 mod S
+__device__ __forceinline__ bool self_conjugate(int u, int v) { return ((u | v) & (S / 2 - 1)) == 0; }
+
 // Lane u writes components GS*j .. GS*j+GS-1 of its row to rowbuf[0..GS-1]
 // (j uniform).
 template <int J>
@@ -876,7 +931,8 @@ template <int B, bool DENSE>
 __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float invW0, int nu, int lane,
                                             int16_t* seq, const float2* __restrict__ scs,
                                             const int (&pm)[TargetPix<B>::P], const int (&pn)[TargetPix<B>::P],
-                                            float (&gacc)[TargetPix<B>::P], float2* gd, float& cr, float& ci) {
+                                            float (&gacc)[TargetPix<B>::P], float2* gd, float& cr, float& ci,
+                                            bool pair = false) {
     cr = gamma * (pk.Rr * invW0);
     ci = gamma * (pk.Ri * invW0);
     if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(pk.u * S + pk.v);
@@ -888,10 +944,12 @@ __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float i
             gd[pk.u * S + pk.v] = gv;
         }
     } else {
+        // a conjugate pair adds Re(c e^{+j theta}) + Re(c* e^{-j theta}) = 2 Re(c e^{+j theta})
+        const float gr = pair ? 2.f * cr : cr, gi = pair ? 2.f * ci : ci;
 #pragma unroll
         for (int q2 = 0; q2 < TargetPix<B>::P; ++q2) {
             const float2 cs = scs[(pk.u * pm[q2] + pk.v * pn[q2]) & (S - 1)];
-            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+            gacc[q2] = fma_rn(gr, cs.x, fma_rn(-gi, cs.y, gacc[q2]));
         }
     }
 }
@@ -900,7 +958,7 @@ __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float i
 // selected, R stays a W + Q (DC phase); at the first other selection a W is
 // folded into Q and the plain loop runs the remaining iterations.  The
 // residual update after the last selection is not needed and not done.
-template <int B, bool DENSE = false>
+template <int B, bool DENSE = false, bool CONJ = false>
 __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* Wd, float2* rowbuf,
                                         const float* __restrict__ swf, const float2* __restrict__ scs,
                                         const BlockState<float>& st, float gamma, int K, int L, int lane,
@@ -929,7 +987,8 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
         pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
         for (;;) {
             pk = argmax_pick<true>(zr, zi, g, Wd, rowbuf, swf, ar, ai, lane);
-            record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci);
+            record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
+                                  CONJ && !self_conjugate(pk.u, pk.v));
             if (++nu == K) return;
             if ((pk.u | pk.v) != 0) break;
             ar -= cr;
@@ -943,10 +1002,17 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
     for (;;) {
         const int s = (S - pk.v) & (S - 1);
         const float2* row = Wd + ((lane - pk.u) & (S - 1)) * WS32;
-        if (s & 1) pass_update<true>(zr, zi, wfr, row, s, cr, ci, g);
-        else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
+        if (CONJ && !self_conjugate(pk.u, pk.v)) {
+            const float2* row2 = Wd + ((lane + pk.u) & (S - 1)) * WS32;
+            if (s & 1) pass_update_pair<true>(zr, zi, wfr, row, s, row2, pk.v, cr, ci, g);
+            else pass_update_pair<false>(zr, zi, wfr, row, s, row2, pk.v, cr, ci, g);
+        } else {
+            if (s & 1) pass_update<true>(zr, zi, wfr, row, s, cr, ci, g);
+            else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
+        }
         pk = argmax_pick<false>(zr, zi, g, Wd, rowbuf, swf, 0.f, 0.f, lane);
-        record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci);
+        record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
+                              CONJ && !self_conjugate(pk.u, pk.v));
         if (++nu == K) return;
     }
 }
@@ -954,7 +1020,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
 // ---------------------------------------------------------------- FP64 loop
 // The debug arithmetic: plain scalar loop with the same representation and
 // selection rule, IEEE division for p.
-template <int B>
+template <int B, bool DENSE_UNUSED = false, bool CONJ = false>
 __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double2* Wd, double2* rowbuf,
                                         const double* __restrict__ swf, const double2* __restrict__ scs,
                                         const BlockState<double>& st, double gamma, int K, int L, int lane,
@@ -999,10 +1065,12 @@ __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double
         const double cr = gamma * (Rr / st.W0);
         const double ci = gamma * (Ri / st.W0);
         if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * S + v);
+        const bool pair = CONJ && !self_conjugate(u, v);
+        const double gr = pair ? 2.0 * cr : cr, gi = pair ? 2.0 * ci : ci;
 #pragma unroll
         for (int q2 = 0; q2 < P; ++q2) {
             const double2 cs = scs[(u * pm[q2] + v * pn[q2]) & (S - 1)];
-            gacc[q2] = fma_rn(cr, cs.x, fma_rn(-ci, cs.y, gacc[q2]));
+            gacc[q2] = fma_rn(gr, cs.x, fma_rn(-gi, cs.y, gacc[q2]));
         }
         if (split) {
             if ((u | v) == 0) {
@@ -1024,6 +1092,20 @@ __device__ __forceinline__ void iterate(double (&zr)[S], double (&zi)[S], double
         }
         const double2* wrow = Wd + ((lane - u) & (S - 1)) * WS + ((S - v) & (S - 1));
         m = 0.0;
+        if (pair) {
+            // conjugate-pair ablation: R -= c W[k-u][l-v] + c* W[k+u][l+v]
+            const double2* wrow2 = Wd + ((lane + u) & (S - 1)) * WS + (v & (S - 1));
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                const double2 w1 = wrow[l], w2 = wrow2[l];
+                const double sr = w1.x + w2.x, si = w1.y + w2.y;
+                const double dr = w1.x - w2.x, di = w1.y - w2.y;
+                zr[l] = fma_rn(-cr, sr, fma_rn(ci, di, zr[l]));
+                zi[l] = fma_rn(-cr, si, fma_rn(-ci, dr, zi[l]));
+                m = fmax(m, objective<double>(zr[l], zi[l], wfr[l <= S / 2 ? l : S - l]));
+            }
+            continue;
+        }
 #pragma unroll
         for (int l = 0; l < S; ++l) {
             const double2 w = wrow[l];
@@ -1104,7 +1186,7 @@ __device__ __forceinline__ void empty_block(int16_t* seq, int K, unsigned long l
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
 // With a tile context the support comes in by TMA; returns false when the
 // bounded wait for it gave up (the warp then stops taking blocks).
-template <typename T, int B, Dft DFT = Dft::SIMT>
+template <typename T, int B, Dft DFT = Dft::SIMT, bool CONJ = false>
 __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
@@ -1153,7 +1235,7 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
         }
     } else {
         if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
-            iterate<B>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
+            iterate<B, false, CONJ>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
             __syncwarp();   // W area free for the next block
         } else if (lane == 0) {
             empty_block(seq, im.K, empty);
@@ -1239,7 +1321,7 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
 
 // Batch form: every warp takes `chunk` consecutive entries of the block list
 // at a time; images are ordered by decreasing K so the long blocks start first.
-template <typename T, int B, int WARPS>
+template <typename T, int B, int WARPS, bool CONJ = false>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
 fsr_batch_kernel(const BatchArgs a) {
     using T2 = typename Vec2<T>::type;
@@ -1289,8 +1371,8 @@ fsr_batch_kernel(const BatchArgs a) {
             tr.bytes = kTileBytes + (unsigned)a.tx_extra;
             tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * warp);
             tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + warp;
-            ok = process_block<T, B>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf,
-                                     nullptr, tr, a.empty, lane);
+            ok = process_block<T, B, Dft::SIMT, CONJ>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf,
+                                                      scs, Wd, rowbuf, nullptr, tr, a.empty, lane);
         }
         if (!ok) break;   // a tile wait gave up: this warp takes no more blocks
     }

@@ -91,6 +91,11 @@ int check_method(fsr_handle* h, const fsr_params* p) {
         return fail(h, FSR_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
     if ((p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32) && p->block != 4)
         return fail(h, FSR_ERR_UNSUPPORTED, "tensor-core transform variants are built for B = 4 only");
+    if (p->update != FSR_UPDATE_SINGLE && p->update != FSR_UPDATE_CONJ_PAIR)
+        return fail(h, FSR_ERR_INVALID_ARG, "update must be FSR_UPDATE_SINGLE or FSR_UPDATE_CONJ_PAIR");
+    if (p->update == FSR_UPDATE_CONJ_PAIR &&
+        (S != fsrk::S || p->block != 4 || (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)))
+        return fail(h, FSR_ERR_UNSUPPORTED, "the conjugate-pair update is built for S = 32, B = 4, FP32 and FP64");
     return FSR_OK;
 }
 
@@ -234,6 +239,8 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
     h->inject_tile_fault = 0;
     const int S = p->block + 2 * p->border;
     if (S != fsrk::S) e = fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, 1, h->sm_count, stream);
+    else if (p->update == FSR_UPDATE_CONJ_PAIR)
+        e = fsrk::launch_batch_conj(a, p->precision == FSR_FP64_DEBUG, h->sm_count, stream);
     else e = fsrk::launch_batch_fp32(a, p->block, sc, h->sm_count, stream);
     // the slot is busy until the stream has passed this point (upload and launch)
     const cudaError_t er = cudaEventRecord(h->single_ev[slot], stream);
@@ -245,7 +252,7 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
 
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                    const fsr_params* p, float* out, cudaStream_t stream) {
-    if (p->precision == FSR_FP32 || p->block + 2 * p->border != fsrk::S)
+    if (p->precision == FSR_FP32 || p->block + 2 * p->border != fsrk::S || p->update == FSR_UPDATE_CONJ_PAIR)
         return enqueue_single_fp32(h, img, mask, height, width, pitch, p, out, stream);
     fsrk::KernelArgs a;
     std::memset(&a, 0, sizeof a);
@@ -345,6 +352,8 @@ cudaError_t launch_batch(const fsrk::BatchArgs& a, const fsr_params* p, fsrk::Sc
     const int S = p->block + 2 * p->border;
     if (S != fsrk::S)
         return fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, sc.chunk, sm_count, s);
+    if (p->update == FSR_UPDATE_CONJ_PAIR)
+        return fsrk::launch_batch_conj(a, p->precision == FSR_FP64_DEBUG, sm_count, s);
     return (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(a, p->block, sc, sm_count, s)
                                              : fsrk::launch_batch_fp32(a, p->block, sc, sm_count, s);
 }
@@ -465,7 +474,8 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
                     cfg->device, prop.major, prop.minor);
     if ((e = fsrk::configure_fp32_batch()) != cudaSuccess || (e = fsrk::configure_small()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
-        (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess)
+        (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess ||
+        (e = fsrk::configure_conj()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));
     fsr_handle* h = new (std::nothrow) fsr_handle();
     if (!h) return fail(nullptr, FSR_ERR_OOM, "host allocation of the handle failed");

@@ -46,6 +46,11 @@ cudaError_t configure_small();
 cudaError_t launch_batch_small(const BatchArgs& a, int S, int B, int fp64, int chunk, int sm_count,
                                cudaStream_t stream);
 
+// Conjugate-pair ablation (S = 32, B = 4; FP32 with kWarpsFp32 warps per
+// CTA, FP64 with 4), batch-table interface.
+cudaError_t configure_conj();
+cudaError_t launch_batch_conj(const BatchArgs& a, int fp64, int sm_count, cudaStream_t stream);
+
 // Warps-per-CTA values instantiated for (precision, B): FP32 has 8 for every
 // B and also 12 and 16 for B = 4; FP64 has 4.
 bool batch_schedule_supported(int fp64, int B, int warps);
@@ -71,9 +76,9 @@ cudaError_t configure_single() {
                                 (int)SmemLayout<T>::bytes(WARPS));
 }
 
-template <typename T, int B, int WARPS>
+template <typename T, int B, int WARPS, bool CONJ = false>
 cudaError_t configure_batch() {
-    return cudaFuncSetAttribute(fsr_batch_kernel<T, B, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fsr_batch_kernel<T, B, WARPS, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)SmemLayout<T>::bytes(WARPS));
 }
 
@@ -87,13 +92,13 @@ cudaError_t launch_single_t(const KernelArgs& a, int sm_count, cudaStream_t stre
     return cudaGetLastError();
 }
 
-template <typename T, int B, int WARPS>
+template <typename T, int B, int WARPS, bool CONJ = false>
 cudaError_t launch_batch_t(const BatchArgs& a, int sm_count, cudaStream_t stream) {
     const size_t smem = SmemLayout<T>::bytes(WARPS);
     int grid = 0;
-    cudaError_t e = persistent_grid(fsr_batch_kernel<T, B, WARPS>, WARPS, smem, a.total, sm_count, &grid);
+    cudaError_t e = persistent_grid(fsr_batch_kernel<T, B, WARPS, CONJ>, WARPS, smem, a.total, sm_count, &grid);
     if (e != cudaSuccess) return e;
-    fsr_batch_kernel<T, B, WARPS><<<grid, WARPS * 32, smem, stream>>>(a);
+    fsr_batch_kernel<T, B, WARPS, CONJ><<<grid, WARPS * 32, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

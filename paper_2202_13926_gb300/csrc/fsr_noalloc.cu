@@ -75,6 +75,8 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
         return report(err, err_len, FSR_ERR_INVALID_ARG, "rho and gamma must be in (0, 1], freq_weight 0 or 1");
     if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
         return report(err, err_len, FSR_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
+    if (p->update != FSR_UPDATE_SINGLE)
+        return report(err, err_len, FSR_ERR_UNSUPPORTED, "the allocation-free entry point runs FSR_UPDATE_SINGLE only");
     for (int i = 0; i < n; ++i) {
         const fsr_image_desc& x = d[i];
         if (!x.img || !x.mask || !x.out || x.height <= 0 || x.width <= 0 || x.pitch < x.width || x.iters < 0 ||

@@ -29,6 +29,8 @@ FSR_TC_BF16X3 = 2
 FSR_TC_TF32 = 3
 PRECISIONS = {"fp32": FSR_FP32, "fp64": FSR_FP64_DEBUG, "tc_bf16x3": FSR_TC_BF16X3,
               "tc_tf32": FSR_TC_TF32}
+FSR_UPDATE_SINGLE, FSR_UPDATE_CONJ_PAIR = 0, 1
+UPDATES = {"single": FSR_UPDATE_SINGLE, "conj_pair": FSR_UPDATE_CONJ_PAIR}
 
 # every function declared in include/fsr.h
 EXPORTED = ("fsr_create", "fsr_destroy", "fsr_last_error", "fsr_reconstruct",
@@ -70,7 +72,7 @@ class fsr_params(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("iters", ctypes.c_int),
                 ("rho", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("freq_weight", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seq_out", ctypes.c_void_p)]
+                ("seq_out", ctypes.c_void_p), ("update", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -148,8 +150,9 @@ def _check(code: int, handle) -> None:
 
 
 def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=True,
-                precision="fp32", seq_out=None) -> fsr_params:
+                precision="fp32", seq_out=None, update="single") -> fsr_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    upd = UPDATES[update] if isinstance(update, str) else int(update)
     seq_ptr = None
     if seq_out is not None:
         import torch
@@ -158,7 +161,7 @@ def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=T
             raise ValueError("seq_out must be a contiguous int16 CUDA tensor")
         seq_ptr = seq_out.data_ptr()
     return fsr_params(int(block), int(border), int(iters), float(rho), float(gamma),
-                      int(bool(freq_weight)), prec, seq_ptr)
+                      int(bool(freq_weight)), prec, seq_ptr, upd)
 
 
 def fsr_num_blocks(height: int, width: int, block: int) -> int:

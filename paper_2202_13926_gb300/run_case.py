@@ -15,6 +15,7 @@ def main(argv=None):
     ap.add_argument("--block", type=int, default=4, help="B")
     ap.add_argument("--iters", type=int, default=100, help="K")
     ap.add_argument("--precision", default="fp32", help="fp32, fp64, tc_bf16x3 or tc_tf32")
+    ap.add_argument("--update", default="single", help="single or conj_pair")
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args(argv)
 
@@ -27,7 +28,7 @@ def main(argv=None):
     d_img, d_mask = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
     d_out = torch.empty_like(d_img)
     params = fsr.make_params(block=args.block, border=(args.support - args.block) // 2, iters=args.iters,
-                             precision=args.precision)
+                             precision=args.precision, update=args.update)
     ms = []
     with fsr.Handle(0) as h:
         for _ in range(args.repeat):
@@ -40,7 +41,7 @@ def main(argv=None):
             ms.append(a.elapsed_time(b))
         h.check_status()
     print(json.dumps({"support": args.support, "block": args.block, "iters": args.iters,
-                      "precision": args.precision, "ms": ms}))
+                      "precision": args.precision, "update": args.update, "ms": ms}))
 
 
 if __name__ == "__main__":
