@@ -262,11 +262,11 @@ def _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torc
 
 
 def _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
-    """Time per 1080p frame and PSNR for support sizes S = 8, 16, 24, 32 (B = 4,
-    L = (S - B) / 2, K = 100; the support-size study of Sec. IV, Fig. 3)."""
+    """Time per 1080p frame and PSNR for support sizes S = 4, 8, 16, 24, 32
+    (B = 4, L = (S - B) / 2, K = 100; the support-size study of Sec. IV, Fig. 3)."""
     truth = d_img.double()
     rows = []
-    for S in (8, 16, 24, 32):
+    for S in (4, 8, 16, 24, 32):
         pm = fsr.make_params(block=B, border=(S - B) // 2, iters=K_ITERS, rho=RHO, gamma=GAMMA)
         for _ in range(2):
             fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)

@@ -82,7 +82,7 @@ typedef struct fsr_config {
 typedef struct fsr_params {
     int block;        /* B: target block size; one of 2, 4, 8, 16 */
     int border;       /* L: border; the support S = B + 2L is 32 (any B), 24 (B in
-                         {4, 8}), 16 (B in {2, 4, 8}) or 8 (B in {2, 4}); S < 32
+                         {4, 8}), 16 (B in {2, 4, 8}), 8 or 4 (B in {2, 4}); S < 32
                          runs FSR_FP32 and FSR_FP64_DEBUG only */
     int iters;        /* K: number of iterations, 0 <= K <= 65535 */
     float rho;        /* rho-hat of Eq. (5), in (0, 1] */

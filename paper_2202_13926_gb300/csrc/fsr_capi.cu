@@ -78,7 +78,7 @@ int check_method(fsr_handle* h, const fsr_params* p) {
     if (S != fsrk::S && !fsrk::small_supported(S, p->block))
         return fail(h, FSR_ERR_UNSUPPORTED,
                     "support B + 2L = %d with B = %d; this library implements S = 32 (B in {2, 4, 8, 16}), "
-                    "S = 24 (B in {4, 8}), S = 16 (B in {2, 4, 8}) and S = 8 (B in {2, 4})",
+                    "S = 24 (B in {4, 8}), S = 16 (B in {2, 4, 8}), S = 8 (B in {2, 4}) and S = 4 (B in {2, 4})",
                     S, p->block);
     if (b_index(p->block) < 0) return fail(h, FSR_ERR_UNSUPPORTED, "block %d not in {2, 4, 8, 16}", p->block);
     if (S != fsrk::S && p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)

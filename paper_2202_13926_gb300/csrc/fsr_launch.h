@@ -39,8 +39,9 @@ cudaError_t launch_batch_fp32(const BatchArgs& a, int B, Schedule sc, int sm_cou
 cudaError_t launch_batch_fp32_sched(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 cudaError_t launch_batch_fp64(const BatchArgs& a, int B, Schedule sc, int sm_count, cudaStream_t stream);
 
-// Small supports S in {8, 16, 24} (FP32 and FP64, batch-table interface):
-// S = 24 with B in {4, 8}, S = 16 with B in {2, 4, 8}, S = 8 with B in {2, 4}.
+// Small supports S in {4, 8, 16, 24} (FP32 and FP64, batch-table interface):
+// S = 24 with B in {4, 8}, S = 16 with B in {2, 4, 8}, S = 8 and S = 4 with
+// B in {2, 4}.
 bool small_supported(int S, int B);
 cudaError_t configure_small();
 cudaError_t launch_batch_small(const BatchArgs& a, int S, int B, int fp64, int chunk, int sm_count,

@@ -1,11 +1,13 @@
 // Small supports S in {8, 16} (the kernel is in fsr_small.cuh); S = 24 is
-// instantiated in fsr_small24.cu.
+// instantiated in fsr_small24.cu, S = 4 (a half-warp per block) is in
+// fsr_tiny.cu.
 #include "fsr_small.cuh"
 
 namespace fsrk {
 
 cudaError_t configure_small24();
 cudaError_t launch_small24(const BatchArgs& a, int B, int fp64, int chunk, int sm_count, cudaStream_t stream);
+cudaError_t launch_tiny(const BatchArgs& a, int B, int fp64, int chunk, int sm_count, cudaStream_t stream);
 
 namespace {
 
@@ -35,7 +37,7 @@ cudaError_t launch_any(const BatchArgs& a, int S, int B, int chunk, int sm_count
 
 bool small_supported(int S, int B) {
     return (S == 24 && (B == 4 || B == 8)) || (S == 16 && (B == 2 || B == 4 || B == 8)) ||
-           (S == 8 && (B == 2 || B == 4));
+           (S == 8 && (B == 2 || B == 4)) || (S == 4 && (B == 2 || B == 4));
 }
 
 cudaError_t configure_small() {
@@ -48,6 +50,7 @@ cudaError_t configure_small() {
 cudaError_t launch_batch_small(const BatchArgs& a, int S, int B, int fp64, int chunk, int sm_count,
                                cudaStream_t stream) {
     if (S == 24) return launch_small24(a, B, fp64, chunk, sm_count, stream);
+    if (S == 4) return launch_tiny(a, B, fp64, chunk, sm_count, stream);
     return fp64 ? launch_any<double>(a, S, B, chunk, sm_count, stream)
                 : launch_any<float>(a, S, B, chunk, sm_count, stream);
 }

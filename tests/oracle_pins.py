@@ -327,10 +327,11 @@ def pin_block_ignores_unknown_values(lib):
 
 
 def pin_small_supports(lib):
-    """The same facts at the support sizes of the support-size study (S = 8,
-    16, 24): spatial-domain residual, exhaustive argmax, exact energy decrease,
-    exact recovery of a cosine and the tiling of an image with L = (S - 4) / 2."""
-    for S_ in (8, 16, 24):
+    """The same facts at the support sizes of the support-size study (S = 4,
+    8, 16, 24): spatial-domain residual, exhaustive argmax, exact energy
+    decrease, exact recovery of a cosine and the tiling of an image with
+    L = (S - 4) / 2."""
+    for S_ in (4, 8, 16, 24):
         wf = lib.freq_weight(S_)
         # exactly Hermitian spectra at every support size (the ties of nu = 0 are exact)
         r0 = lib.fsr_block(*_rand_block(60 + S_, S=S_), K=1)

@@ -48,3 +48,13 @@ def sequence_mismatches(seq_gpu, seq_ref, margin_ref):
         else:
             n_hard += 1
     return n_hard, n_tie
+
+
+def same_sequence_pixels(seq_gpu, seq_ref, H, W, B):
+    """H x W flags: pixels of target blocks whose selection sequences are
+    identical on both sides (a tie-class divergence legitimately changes the
+    values of its block; value comparisons of the FP64 path use these)."""
+    same = np.all(np.asarray(seq_gpu).astype(np.int64) == np.asarray(seq_ref).astype(np.int64), axis=1)
+    nbx, nby = -(-W // B), -(-H // B)
+    blocks = same.reshape(nby, nbx)
+    return np.kron(blocks, np.ones((B, B), bool))[:H, :W]

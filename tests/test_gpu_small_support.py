@@ -1,5 +1,6 @@
-"""Supports smaller than 32 (S = B + 2L in {8, 16, 24}; the support-size study
-of Sec. IV): the small-support kernel against the FP64 oracle, which takes any S."""
+"""Supports smaller than 32 (S = B + 2L in {4, 8, 16, 24}; the support-size
+study of Sec. IV): the small-support kernels against the FP64 oracle, which
+takes any S."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CASES = [(24, 4), (24, 8), (16, 4), (16, 2), (16, 8), (8, 4), (8, 2)]   # (S, B)
+CASES = [(24, 4), (24, 8), (16, 4), (16, 2), (16, 8), (8, 4), (8, 2), (4, 4), (4, 2)]   # (S, B)
 
 
 @pytest.fixture(scope="module")
@@ -69,20 +70,22 @@ def test_fp64_selection_sequences(handle, S, B):
     ref, r = _oracle(img, mask, S, B, 60)
     n_hard, n_tie = PA.sequence_mismatches(seq, r["seq"], r["margin"])
     assert n_hard == 0, (S, B, n_hard, n_tie)
-    assert np.max(np.abs(got - ref)) <= 1e-3
+    same = PA.same_sequence_pixels(seq, r["seq"], img.shape[0], img.shape[1], B)
+    assert np.max(np.abs(got - ref)[same]) <= 1e-3
 
 
 @pytest.mark.parametrize("H,W", [(1, 1), (5, 7), (37, 53), (70, 9)])
 def test_ragged_sizes_and_edges(handle, H, W):
     img = synth.sinusoid_image(H, W, seed=H * 7 + W)
     mask = synth.iid_mask(H, W, seed=H + W, missing=0.6)
-    for S, B in ((24, 4), (16, 4), (8, 2)):
+    for S, B in ((24, 4), (16, 4), (8, 2), (4, 4), (4, 2)):
         got, seq = _run(handle, img, mask, S, B, 20, precision="fp64", seq=True)
         ref, r = _oracle(img, mask, S, B, 20)
         assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
         n_hard, _ = PA.sequence_mismatches(seq, r["seq"], r["margin"])
         assert n_hard == 0, (H, W, S, B)
-        assert np.max(np.abs(got - ref)) <= 1e-3
+        same = PA.same_sequence_pixels(seq, r["seq"], H, W, B)
+        assert np.max(np.abs(got - ref)[same], initial=0.0) <= 1e-3
 
 
 def test_empty_supports_and_batch_form(fsr_mod, handle):
