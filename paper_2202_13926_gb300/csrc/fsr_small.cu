@@ -1,6 +1,7 @@
 // Small supports S in {8, 16} (the kernel is in fsr_small.cuh); S = 24 is
 // instantiated in fsr_small24.cu, S = 4 (a half-warp per block) is in
-// fsr_tiny.cu.
+// fsr_tiny.cu, and FP32 at S = 16 runs the half-warp FFT kernel of
+// fsr_s16.cu (FP64 at S = 16 runs the kernel of fsr_small.cuh).
 #include "fsr_small.cuh"
 
 namespace fsrk {
@@ -8,6 +9,8 @@ namespace fsrk {
 cudaError_t configure_small24();
 cudaError_t launch_small24(const BatchArgs& a, int B, int fp64, int chunk, int sm_count, cudaStream_t stream);
 cudaError_t launch_tiny(const BatchArgs& a, int B, int fp64, int chunk, int sm_count, cudaStream_t stream);
+cudaError_t configure_s16();
+cudaError_t launch_s16(const BatchArgs& a, int B, int chunk, int sm_count, cudaStream_t stream);
 
 namespace {
 
@@ -44,6 +47,7 @@ cudaError_t configure_small() {
     cudaError_t e = configure_all<float>();
     if (e != cudaSuccess) return e;
     if ((e = configure_all<double>()) != cudaSuccess) return e;
+    if ((e = configure_s16()) != cudaSuccess) return e;
     return configure_small24();
 }
 
@@ -51,6 +55,7 @@ cudaError_t launch_batch_small(const BatchArgs& a, int S, int B, int fp64, int c
                                cudaStream_t stream) {
     if (S == 24) return launch_small24(a, B, fp64, chunk, sm_count, stream);
     if (S == 4) return launch_tiny(a, B, fp64, chunk, sm_count, stream);
+    if (S == 16 && !fp64) return launch_s16(a, B, chunk, sm_count, stream);
     return fp64 ? launch_any<double>(a, S, B, chunk, sm_count, stream)
                 : launch_any<float>(a, S, B, chunk, sm_count, stream);
 }
