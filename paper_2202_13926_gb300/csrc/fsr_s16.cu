@@ -257,8 +257,9 @@ __device__ __forceinline__ void block16(const ImageArgs& im, long long blk, bool
 
     for (int nu = 0; nu < Kmax; ++nu) {   // uniform over the warp
         const bool run = active && nu < Kh;
-        // a5: block maximum, the lowest row holding it, then its lowest column
-        const unsigned Mb = half_max(run ? __float_as_uint(m_lane) : 0u);
+        // a5: block maximum (each half reduces over its own 16 lanes), the
+        // lowest row holding it, then its lowest column
+        const unsigned Mb = __reduce_max_sync(0xFFFFu << hb, run ? __float_as_uint(m_lane) : 0u);
         const unsigned ub = (__ballot_sync(FULL, run && __float_as_uint(m_lane) == Mb) >> hb) & 0xFFFFu;
         const int u = ub ? __ffs(ub) - 1 : 0;
         __syncwarp();   // the previous pick's reads of the published row are done
