@@ -14,13 +14,16 @@ cudaError_t launch_s16(const BatchArgs& a, int B, int chunk, int sm_count, cudaS
 
 namespace {
 
+// S = 16 is instantiated here for FP64 only (FP32 runs fsr_s16.cu).
 template <typename T>
 cudaError_t configure_all() {
     using namespace small;
     cudaError_t e;
-    if ((e = configure_one<T, 16, 2>()) != cudaSuccess) return e;
-    if ((e = configure_one<T, 16, 4>()) != cudaSuccess) return e;
-    if ((e = configure_one<T, 16, 8>()) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 8) {
+        if ((e = configure_one<T, 16, 2>()) != cudaSuccess) return e;
+        if ((e = configure_one<T, 16, 4>()) != cudaSuccess) return e;
+        if ((e = configure_one<T, 16, 8>()) != cudaSuccess) return e;
+    }
     if ((e = configure_one<T, 8, 2>()) != cudaSuccess) return e;
     return configure_one<T, 8, 4>();
 }
@@ -28,9 +31,11 @@ cudaError_t configure_all() {
 template <typename T>
 cudaError_t launch_any(const BatchArgs& a, int S, int B, int chunk, int sm_count, cudaStream_t stream) {
     using namespace small;
-    if (S == 16 && B == 2) return launch_one<T, 16, 2>(a, chunk, sm_count, stream);
-    if (S == 16 && B == 4) return launch_one<T, 16, 4>(a, chunk, sm_count, stream);
-    if (S == 16 && B == 8) return launch_one<T, 16, 8>(a, chunk, sm_count, stream);
+    if constexpr (sizeof(T) == 8) {
+        if (S == 16 && B == 2) return launch_one<T, 16, 2>(a, chunk, sm_count, stream);
+        if (S == 16 && B == 4) return launch_one<T, 16, 4>(a, chunk, sm_count, stream);
+        if (S == 16 && B == 8) return launch_one<T, 16, 8>(a, chunk, sm_count, stream);
+    }
     if (S == 8 && B == 2) return launch_one<T, 8, 2>(a, chunk, sm_count, stream);
     if (S == 8 && B == 4) return launch_one<T, 8, 4>(a, chunk, sm_count, stream);
     return cudaErrorNotSupported;
