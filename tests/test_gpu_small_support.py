@@ -126,3 +126,31 @@ def test_unsupported_support_sizes_are_rejected(fsr_mod, handle):
         with pytest.raises(fsr.FsrError) as e:
             handle.reconstruct(ti, tm, **kw)
         assert e.value.code == fsr.FSR_ERR_UNSUPPORTED, kw
+
+
+@pytest.mark.parametrize("S,B", [(16, 4), (16, 2), (16, 8), (4, 4), (4, 2), (8, 4), (24, 4)])
+def test_fp32_batch_of_ragged_images_with_mixed_K(fsr_mod, handle, S, B):
+    """A batch of ragged images with different K (the S = 16 and S = 4
+    kernels pair two blocks per warp, also across images with different K):
+    every image equals its single-image call bit for bit, and the oracle."""
+    fsr = fsr_mod
+    dev = torch.device("cuda:0")
+    specs = [((17, 17), 40), ((1, 1), 13), ((37, 21), 0), ((13, 17), 25)]
+    items = []
+    for i, ((H, W), K) in enumerate(specs):
+        img = synth.sinusoid_image(H, W, seed=90 + i)
+        mk = synth.iid_mask(H, W, seed=95 + i, missing=0.5)
+        ti, tm = torch.from_numpy(img).to(dev), torch.from_numpy(mk).to(dev)
+        items.append((img, mk, K, ti, tm, torch.full_like(ti, -1.0)))
+    p = fsr.make_params(block=B, border=(S - B) // 2, iters=40)
+    fsr.fsr_reconstruct_batch(handle.ptr, [fsr.image_desc(ti, tm, to, K) for _, _, K, ti, tm, to in items], p)
+    torch.cuda.synchronize()
+    gots, refs = [], []
+    for img, mk, K, ti, tm, to in items:
+        got = to.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, _run(handle, img, mk, S, B, K)), (img.shape, K)
+        assert np.array_equal(got[mk == 1], img[mk == 1].astype(np.float64))
+        ref, _ = _oracle(img, mk, S, B, K)
+        gots.append(got.ravel())
+        refs.append(ref.ravel())
+    assert PA.frac_within(np.concatenate(gots), np.concatenate(refs)) >= 0.99
