@@ -1,5 +1,6 @@
-// FSR with the 4 x 4 support (S = 4: B = 4 with L = 0, or B = 2 with L = 1),
-// the smallest support of the support-size study (Sec. IV, Fig. 3).  One
+// FP64 FSR with the 4 x 4 support (S = 4: B = 4 with L = 0, or B = 2 with
+// L = 1), the smallest support of the support-size study (Sec. IV, Fig. 3);
+// FP32 at S = 4 runs the group kernel of fsr_group.cu.  One
 // half-warp per block: lane t of the half holds pixel (t / 4, t % 4) and
 // spectrum component (k, l) = (t / 4, t % 4).  The 2-D DFTs of Eq. (7) are
 // direct sums over the 16 pixels, fetched by shuffles, with the exact fourth
@@ -171,11 +172,9 @@ cudaError_t launch_one(const BatchArgs& a, int chunk, int sm_count, cudaStream_t
 
 }  // namespace
 
-cudaError_t launch_tiny(const BatchArgs& a, int B, int fp64, int chunk, int sm_count, cudaStream_t stream) {
-    if (B == 4) return fp64 ? launch_one<double, 4>(a, chunk, sm_count, stream)
-                            : launch_one<float, 4>(a, chunk, sm_count, stream);
-    if (B == 2) return fp64 ? launch_one<double, 2>(a, chunk, sm_count, stream)
-                            : launch_one<float, 2>(a, chunk, sm_count, stream);
+cudaError_t launch_tiny(const BatchArgs& a, int B, int chunk, int sm_count, cudaStream_t stream) {
+    if (B == 4) return launch_one<double, 4>(a, chunk, sm_count, stream);
+    if (B == 2) return launch_one<double, 2>(a, chunk, sm_count, stream);
     return cudaErrorNotSupported;
 }
 
