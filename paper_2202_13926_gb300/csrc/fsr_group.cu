@@ -1,4 +1,4 @@
-// FP32 FSR with a support S in {4, 16} (B <= S; the support-size study of
+// FP32 FSR with a support S in {4, 8, 16} (B <= S; the support-size study of
 // Sec. IV, Figs. 3 and 5): one group of S lanes per block, 32 / S blocks per
 // warp.  Lane t of a group holds column t of the support, then row t of the
 // spectrum (S complex values in registers), as the S = 32 kernel does with a
@@ -365,8 +365,14 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     }
 }
 
+// CTAs per SM the register budget is set for: 16 warps per SM at S = 16
+// (<= 128 registers), 24 at S = 8 (<= 85), 32 at S = 4 (<= 64).  Measured on
+// the 1080p frame: S = 4 0.53 ms with 16 warps per SM, 0.39 ms with 32;
+// S = 8 0.91 ms with 16, 0.78 ms with 24 (32 spills registers).
+template <int SZ> constexpr int group_min_ctas() { return SZ == 4 ? 4 : SZ == 8 ? 3 : 2; }
+
 template <int SZ, int B, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) fsr_group_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_kernel(const BatchArgs a) {
     using G = Grp<SZ>;
     extern __shared__ __align__(128) unsigned char smem[];
     float* sw0 = reinterpret_cast<float*>(smem + G::w0_off);
@@ -458,15 +464,19 @@ cudaError_t configure_group() {
     if ((e = configure_one<16, 2>()) != cudaSuccess) return e;
     if ((e = configure_one<16, 4>()) != cudaSuccess) return e;
     if ((e = configure_one<16, 8>()) != cudaSuccess) return e;
+    if ((e = configure_one<8, 2>()) != cudaSuccess) return e;
+    if ((e = configure_one<8, 4>()) != cudaSuccess) return e;
     if ((e = configure_one<4, 2>()) != cudaSuccess) return e;
     return configure_one<4, 4>();
 }
 
-// FP32, S in {4, 16} (the template also covers S = 8)
+// FP32, S in {4, 8, 16}
 cudaError_t launch_group(const BatchArgs& a, int S, int B, int chunk, int sm_count, cudaStream_t stream) {
     if (S == 16 && B == 2) return launch_one<16, 2>(a, chunk, sm_count, stream);
     if (S == 16 && B == 4) return launch_one<16, 4>(a, chunk, sm_count, stream);
     if (S == 16 && B == 8) return launch_one<16, 8>(a, chunk, sm_count, stream);
+    if (S == 8 && B == 2) return launch_one<8, 2>(a, chunk, sm_count, stream);
+    if (S == 8 && B == 4) return launch_one<8, 4>(a, chunk, sm_count, stream);
     if (S == 4 && B == 2) return launch_one<4, 2>(a, chunk, sm_count, stream);
     if (S == 4 && B == 4) return launch_one<4, 4>(a, chunk, sm_count, stream);
     return cudaErrorNotSupported;
