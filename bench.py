@@ -406,11 +406,11 @@ def _measure_serving(fsr, handle, torch, seconds: float):
     return summ
 
 
-def _measure_stream(fsr, handle, torch, img, mask, n: int = 60):
+def _measure_stream(fsr, handle, torch, img, mask, n: int = 60, support: int = 32):
     """Frame streaming end to end: n 1080p frames (host buffers, pinned)
     submitted at once to the serving loop, which overlaps the host-to-device
     copies, the launches and the copies back (the paper's end-to-end frame
-    rate setting)."""
+    rate setting; its Fig. 5 uses the support S = 16)."""
     from paper_2202_13926_gb300 import serving
     hi = torch.from_numpy(img).pin_memory()
     hm = torch.from_numpy(mask).pin_memory()
@@ -428,13 +428,14 @@ def _measure_stream(fsr, handle, torch, img, mask, n: int = 60):
             return self.srv.poll(wait_ms)
 
     with fsr.Server(handle, pool_bytes=1 << 30, max_inflight=8, streams=2,
-                    block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
+                    block=B, border=(support - B) // 2, rho=RHO, gamma=GAMMA) as srv:
         serving.run_stream(_Reuse(srv), [(hi, hm)], np.zeros(4), np.zeros(4, int), np.full(4, K_ITERS))
         res = serving.run_stream(_Reuse(srv), [(hi, hm)], np.zeros(n), np.zeros(n, int), np.full(n, K_ITERS))
     mp = H * W / 1e6
     return {"frames": n, "wall_s": res["wall_s"], "fps": n / res["wall_s"], "mp_per_s": n * mp / res["wall_s"],
             "h2d_bytes_per_frame": int(img.nbytes + mask.nbytes), "d2h_bytes_per_frame": int(img.nbytes),
-            "workload": "1920x1080 quarter sampling, K = 100, all frames submitted at t = 0, 8 in flight"}
+            "workload": f"1920x1080 quarter sampling, S = {support}, K = 100, all frames submitted at t = 0, "
+                        "8 in flight"}
 
 
 def _config():
@@ -584,6 +585,7 @@ def main():
         line["batch"] = _measure_batch(fsr, handle, dev, torch)
     if world == 1 and args.serve_seconds > 0:
         line["frame_stream"] = _measure_stream(fsr, handle, torch, img, mask)
+        line["frame_stream_S16"] = _measure_stream(fsr, handle, torch, img, mask, support=16)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = _measure_serving(fsr, handle, torch, args.serve_seconds)
 
