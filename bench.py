@@ -376,7 +376,7 @@ def _measure_batch(fsr, handle, dev, torch):
             "graph": True}
 
 
-def _measure_serving(fsr, handle, torch, seconds: float):
+def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 2):
     """Poisson stream, mean 120 req/s: 720p/1080p/4K frames, quarter sampling or
     macroblock loss, K in {50, 100}, through the continuous-batching server."""
     from paper_2202_13926_gb300 import serving, synth
@@ -394,14 +394,14 @@ def _measure_serving(fsr, handle, torch, seconds: float):
     rng = np.random.default_rng(10)
     kinds = rng.integers(0, len(frames), arr.size)
     iters = rng.choice([50, 100], arr.size)
-    with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=2,
+    with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=streams,
                     block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
         res = serving.run_stream(srv, frames, arr, kinds, iters)
         st = srv.stats()
     res["kinds"] = np.asarray([cls[k] for k in kinds])
     summ = serving.summarize(res, [n for n, _, _ in sizes], {i: mps[2 * i] for i in range(3)})
     summ.update({"rate_hz": 120.0, "duration_s": seconds, "launches": st["launches"],
-                 "peak_pool_bytes": st["peak_pool_bytes"], "frame_period_ms": 1000.0 / 60.0,
+                 "peak_pool_bytes": st["peak_pool_bytes"], "frame_period_ms": 1000.0 / 60.0, "streams": streams,
                  "workload": "Poisson arrivals, 720p/1080p/4K x quarter/macroblock masks, K in {50,100}"})
     return summ
 

@@ -240,11 +240,15 @@ int fsr_set_schedule(fsr_handle *h, int block, int precision, const fsr_schedule
  * fsr_server_submit queues a request (HOST buffers) and returns at once.  The
  * worker admits queued requests in arrival order while the pool has room for
  * their image, mask and output and a slot is free, starts their host-to-device
- * copies, and launches every admitted, not yet launched request together as
- * one batch (fsr_reconstruct_batch's kernel) on the next of its compute
- * streams: requests that arrive while others run join the next launch, and
+ * copies, and launches the admitted, not yet launched requests as batches
+ * (fsr_reconstruct_batch's kernel): requests of at most 1920 x 1088 pixels
+ * together on the first compute stream, which has the highest stream
+ * priority (or on any free stream), larger ones together on the other
+ * streams.  Requests that arrive while others run join the next launch, and
  * launches, copies in and copies out of different requests overlap on the
- * device.  A finished request's output is copied back to its host buffer, its
+ * device.  With S = 32 the server's launches run short-lived CTAs (each warp
+ * takes one chunk of blocks), so the blocks of a launch of small
+ * requests start as soon as CTAs of a running launch of large ones finish.  A finished request's output is copied back to its host buffer, its
  * pool memory is released, and its latency (submit to output on the host) is
  * recorded.  Results do not depend on what else is in flight: every block is
  * computed by one warp with the arithmetic of fsr_reconstruct. */

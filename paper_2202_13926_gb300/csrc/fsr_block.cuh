@@ -107,6 +107,8 @@ struct BatchArgs {
     const TileMaps* maps = nullptr;        // optional: n tile descriptors (device, 64-byte aligned)
     unsigned* status = nullptr;            // device status word (needed with maps)
     int tx_extra = 0;                      // test hook of the tile wait (0 in use)
+    int one_round = 0;                     // 1: run the ONE_ROUND form of the FP32 S = 32 batch kernel
+                                           // (a warp takes one chunk, then its CTA ends)
 };
 
 // cos(pi t / 16) for t = 0..8 (mathematical constants).
@@ -1321,7 +1323,10 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
 
 // Batch form: every warp takes `chunk` consecutive entries of the block list
 // at a time; images are ordered by decreasing K so the long blocks start first.
-template <typename T, int B, int WARPS, bool CONJ = false>
+// ONE_ROUND: short-lived CTAs (a warp takes one chunk; the grid is sized to
+// the work), used by the serving loop so that the CTAs of a launch on a
+// higher-priority stream are scheduled as soon as running CTAs finish.
+template <typename T, int B, int WARPS, bool CONJ = false, bool ONE_ROUND = false>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
 fsr_batch_kernel(const BatchArgs a) {
     using T2 = typename Vec2<T>::type;
@@ -1375,6 +1380,7 @@ fsr_batch_kernel(const BatchArgs a) {
                                                       scs, Wd, rowbuf, nullptr, tr, a.empty, lane);
         }
         if (!ok) break;   // a tile wait gave up: this warp takes no more blocks
+        if constexpr (ONE_ROUND) break;
     }
 }
 

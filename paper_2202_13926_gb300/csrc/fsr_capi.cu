@@ -354,6 +354,7 @@ cudaError_t launch_batch(const fsrk::BatchArgs& a, const fsr_params* p, fsrk::Sc
         return fsrk::launch_batch_small(a, S, p->block, p->precision == FSR_FP64_DEBUG, sc.chunk, sm_count, s);
     if (p->update == FSR_UPDATE_CONJ_PAIR)
         return fsrk::launch_batch_conj(a, p->precision == FSR_FP64_DEBUG, sm_count, s);
+    if (a.one_round && p->precision == FSR_FP32) return fsrk::launch_batch_fp32_short(a, p->block, s);
     return (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(a, p->block, sc, sm_count, s)
                                              : fsrk::launch_batch_fp32(a, p->block, sc, sm_count, s);
 }
@@ -475,7 +476,7 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
     if ((e = fsrk::configure_fp32_batch()) != cudaSuccess || (e = fsrk::configure_small()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
         (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess ||
-        (e = fsrk::configure_conj()) != cudaSuccess)
+        (e = fsrk::configure_conj()) != cudaSuccess || (e = fsrk::configure_fp32_short()) != cudaSuccess)
         return fail(nullptr, FSR_ERR_CUDA, "configuring kernels: %s", cudaGetErrorString(e));
     fsr_handle* h = new (std::nothrow) fsr_handle();
     if (!h) return fail(nullptr, FSR_ERR_OOM, "host allocation of the handle failed");

@@ -47,6 +47,11 @@ cudaError_t configure_small();
 cudaError_t launch_batch_small(const BatchArgs& a, int S, int B, int fp64, int chunk, int sm_count,
                                cudaStream_t stream);
 
+// Short-lived-CTA form of the FP32 batch kernel (kWarpsFp32 warps, any B),
+// for launches with a.one_round set (the serving loop).
+cudaError_t configure_fp32_short();
+cudaError_t launch_batch_fp32_short(const BatchArgs& a, int B, cudaStream_t stream);
+
 // Conjugate-pair ablation (S = 32, B = 4; FP32 with kWarpsFp32 warps per
 // CTA, FP64 with 4), batch-table interface.
 cudaError_t configure_conj();
@@ -77,10 +82,10 @@ cudaError_t configure_single() {
                                 (int)SmemLayout<T>::bytes(WARPS));
 }
 
-template <typename T, int B, int WARPS, bool CONJ = false>
+template <typename T, int B, int WARPS, bool CONJ = false, bool ONE_ROUND = false>
 cudaError_t configure_batch() {
-    return cudaFuncSetAttribute(fsr_batch_kernel<T, B, WARPS, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SmemLayout<T>::bytes(WARPS));
+    return cudaFuncSetAttribute(fsr_batch_kernel<T, B, WARPS, CONJ, ONE_ROUND>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SmemLayout<T>::bytes(WARPS));
 }
 
 template <typename T, int B, int WARPS>
@@ -93,13 +98,20 @@ cudaError_t launch_single_t(const KernelArgs& a, int sm_count, cudaStream_t stre
     return cudaGetLastError();
 }
 
-template <typename T, int B, int WARPS, bool CONJ = false>
+template <typename T, int B, int WARPS, bool CONJ = false, bool ONE_ROUND = false>
 cudaError_t launch_batch_t(const BatchArgs& a, int sm_count, cudaStream_t stream) {
     const size_t smem = SmemLayout<T>::bytes(WARPS);
     int grid = 0;
-    cudaError_t e = persistent_grid(fsr_batch_kernel<T, B, WARPS, CONJ>, WARPS, smem, a.total, sm_count, &grid);
+    cudaError_t e = cudaSuccess;
+    if constexpr (ONE_ROUND) {   // short-lived CTAs: one chunk per warp
+        const long long per_cta = (long long)WARPS * a.chunk;
+        const long long g = (a.total + per_cta - 1) / per_cta;
+        grid = (int)(g < 1 ? 1 : (g > 0x7fffffffll ? 0x7fffffffll : g));
+    } else {
+        e = persistent_grid(fsr_batch_kernel<T, B, WARPS, CONJ>, WARPS, smem, a.total, sm_count, &grid);
+    }
     if (e != cudaSuccess) return e;
-    fsr_batch_kernel<T, B, WARPS, CONJ><<<grid, WARPS * 32, smem, stream>>>(a);
+    fsr_batch_kernel<T, B, WARPS, CONJ, ONE_ROUND><<<grid, WARPS * 32, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,12 @@ using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxBatch = 256;   // requests per launch at most
+// Requests of at most this many pixels (1080p and smaller) are the short
+// class: launched on the high-priority stream of slot 0.
+constexpr long long kShortPixels = 1920ll * 1088ll;
+// S = 32 launches of the server run short-lived CTAs (a warp takes one chunk
+// of blocks), so that the CTAs of a short-class launch are scheduled as soon
+// as CTAs of a running long launch finish.
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -151,6 +157,59 @@ void finish(fsr_server* s, Request* r, Clock::time_point now) {
     delete r;
 }
 
+// Launches up to kMaxBatch of the requests in q (taken from its front) as
+// one batch on the given free slot; the rest stay in q.  Returns false when
+// the launch table does not fit in the pool now (nothing launched).
+bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q) {
+    const int n = (int)std::min<size_t>(q.size(), kMaxBatch);
+    Launch& L = s->launches[slot];
+    size_t toff = 0;
+    const size_t tbytes = fsri::table_bytes(n);
+    if (!s->alloc->alloc(tbytes, &toff)) return false;
+    std::vector<Request*> batch(q.begin(), q.begin() + n);
+    q.erase(q.begin(), q.begin() + n);
+    std::vector<fsr_image_desc> d(n);
+    for (int j = 0; j < n; ++j) {
+        Request* r = batch[j];
+        const size_t npix = (size_t)r->H * r->W;
+        d[j].img = reinterpret_cast<const float*>(s->pool + r->off);
+        d[j].mask = s->pool + r->off + mask_offset(npix);
+        d[j].out = reinterpret_cast<float*>(s->pool + r->off + out_offset(npix));
+        d[j].height = r->H;
+        d[j].width = r->W;
+        d[j].pitch = r->W;
+        d[j].iters = r->K;
+        d[j].seq_out = nullptr;
+    }
+    // (errors go to this thread's own record, not to the handle the caller uses)
+    const long long total = fsri::build_table(nullptr, n, d.data(), &s->p, s->h_tables[slot]);
+    cudaStream_t cs = s->s_comp[slot];
+    cudaError_t e = total < 0 ? cudaErrorInvalidValue : cudaSuccess;
+    for (Request* r : batch)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, r->ev, 0);
+    void* dt = s->pool + toff;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, s->h_tables[slot], tbytes, cudaMemcpyHostToDevice, cs);
+    const fsrk::Schedule sc = s->h->sched[s->p.precision][fsri::b_index(s->p.block)];
+    if (e == cudaSuccess) {
+        fsrk::BatchArgs a = fsri::batch_args(s->h, dt, n, total, &s->p, sc.chunk);
+        if (s->p.block + 2 * s->p.border == fsrk::S) a.one_round = 1;
+        e = fsri::launch_batch(a, &s->p, sc, s->h->sm_count, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(L.done, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (Request* r : batch) r->failed = true;
+        cudaEventRecord(L.done, cs);
+    }
+    for (Request* r : batch) r->st = St::Launched;
+    L.reqs = batch;
+    L.table_off = toff;
+    L.table_bytes = tbytes;
+    L.active = true;
+    s->n_launches += 1;
+    return true;
+}
+
 // One pass of the worker over completions, admissions and launches (lock held).
 bool step(fsr_server* s) {
     bool progressed = false;
@@ -216,74 +275,41 @@ bool step(fsr_server* s) {
         s->admitted.push_back(r);
         progressed = true;
     }
-    // 4. launch everything admitted on a free compute slot (continuous batching)
+    // 4. launch the admitted requests (continuous batching): the short class
+    //    on slot 0 (high-priority stream) or any free slot, the long class
+    //    on the other slots
     if (!s->admitted.empty()) {
-        int slot = -1;
-        for (int i = 0; i < s->nstreams; ++i)
-            if (!s->launches[i].active) {
-                slot = i;
-                break;
+        std::vector<Request*> shortq, longq;
+        for (Request* r : s->admitted) {
+            if (r->failed) {
+                r->st = St::CopyingOut;
+                s->out_pending.push_back(r);
+            } else if ((long long)r->H * r->W <= kShortPixels) {
+                shortq.push_back(r);
+            } else {
+                longq.push_back(r);
             }
-        if (slot >= 0) {
-            std::vector<Request*> batch;
-            std::vector<Request*> rest;
-            for (Request* r : s->admitted) {
-                if (r->failed) {
-                    r->st = St::CopyingOut;
-                    s->out_pending.push_back(r);
-                } else if ((int)batch.size() < kMaxBatch) {
-                    batch.push_back(r);
-                } else {
-                    rest.push_back(r);
-                }
-            }
-            s->admitted.swap(rest);
-            Launch& L = s->launches[slot];
-            size_t toff = 0;
-            const int n = (int)batch.size();
-            const size_t tbytes = n ? fsri::table_bytes(n) : 0;
-            if (n && !s->alloc->alloc(tbytes, &toff)) {
-                s->admitted.insert(s->admitted.begin(), batch.begin(), batch.end());   // retry later
-            } else if (n) {
-                std::vector<fsr_image_desc> d(n);
-                for (int j = 0; j < n; ++j) {
-                    Request* r = batch[j];
-                    const size_t npix = (size_t)r->H * r->W;
-                    d[j].img = reinterpret_cast<const float*>(s->pool + r->off);
-                    d[j].mask = s->pool + r->off + mask_offset(npix);
-                    d[j].out = reinterpret_cast<float*>(s->pool + r->off + out_offset(npix));
-                    d[j].height = r->H;
-                    d[j].width = r->W;
-                    d[j].pitch = r->W;
-                    d[j].iters = r->K;
-                    d[j].seq_out = nullptr;
-                }
-                // (errors go to this thread's own record, not to the handle the caller uses)
-                const long long total = fsri::build_table(nullptr, n, d.data(), &s->p, s->h_tables[slot]);
-                cudaStream_t cs = s->s_comp[slot];
-                cudaError_t e = total < 0 ? cudaErrorInvalidValue : cudaSuccess;
-                for (Request* r : batch)
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, r->ev, 0);
-                void* dt = s->pool + toff;
-                if (e == cudaSuccess) e = cudaMemcpyAsync(dt, s->h_tables[slot], tbytes, cudaMemcpyHostToDevice, cs);
-                const fsrk::Schedule sc = s->h->sched[s->p.precision][fsri::b_index(s->p.block)];
-                if (e == cudaSuccess)
-                    e = fsri::launch_batch(fsri::batch_args(s->h, dt, n, total, &s->p, sc.chunk), &s->p, sc,
-                                           s->h->sm_count, cs);
-                if (e == cudaSuccess) e = cudaEventRecord(L.done, cs);
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    for (Request* r : batch) r->failed = true;
-                    cudaEventRecord(L.done, cs);
-                }
-                for (Request* r : batch) r->st = St::Launched;
-                L.reqs = batch;
-                L.table_off = toff;
-                L.table_bytes = tbytes;
-                L.active = true;
-                s->n_launches += 1;
-                progressed = true;
-            }
+        }
+        s->admitted.clear();
+        auto free_slot = [&](bool allow0, bool allow_rest) {
+            if (allow0 && !s->launches[0].active) return 0;
+            if (allow_rest)
+                for (int i = 1; i < s->nstreams; ++i)
+                    if (!s->launches[i].active) return i;
+            return -1;
+        };
+        const bool many = s->nstreams > 1;
+        // what is not launched now (no free slot, no room for the table, or
+        // beyond kMaxBatch) waits in the admitted list for the next pass
+        if (!shortq.empty()) {
+            const int slot = free_slot(true, true);
+            if (slot >= 0 && launch_on(s, slot, shortq)) progressed = true;
+            s->admitted.insert(s->admitted.end(), shortq.begin(), shortq.end());
+        }
+        if (!longq.empty()) {
+            const int slot = free_slot(!many, many);
+            if (slot >= 0 && launch_on(s, slot, longq)) progressed = true;
+            s->admitted.insert(s->admitted.end(), longq.begin(), longq.end());
         }
     }
     return progressed;
@@ -343,8 +369,14 @@ int fsr_server_create(fsr_handle* h, const fsr_server_config* cfg, const fsr_par
     s->s_comp.resize(s->nstreams, nullptr);
     s->h_tables.resize(s->nstreams, nullptr);
     s->launches.resize(s->nstreams);
+    int prio_low = 0, prio_high = 0;   // numerically lower = higher priority
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
     for (int i = 0; i < s->nstreams && okk; ++i) {
-        okk = cudaStreamCreateWithFlags(&s->s_comp[i], cudaStreamNonBlocking) == cudaSuccess &&
+        okk = cudaStreamCreateWithPriority(&s->s_comp[i], cudaStreamNonBlocking, i == 0 ? prio_high : prio_low) ==
+                  cudaSuccess &&
               cudaMallocHost(&s->h_tables[i], fsri::table_bytes(kMaxBatch)) == cudaSuccess &&
               cudaEventCreateWithFlags(&s->launches[i].done, cudaEventDisableTiming) == cudaSuccess;
         s->launches[i].slot = i;
