@@ -396,11 +396,14 @@ def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 2):
     iters = rng.choice([50, 100], arr.size)
     with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=streams,
                     block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
+        warm = arr < 1.0   # the first second of the same stream, untimed
+        serving.run_stream(srv, frames, arr[warm], kinds[warm], iters[warm])
+        launches0 = srv.stats()["launches"]
         res = serving.run_stream(srv, frames, arr, kinds, iters)
         st = srv.stats()
     res["kinds"] = np.asarray([cls[k] for k in kinds])
     summ = serving.summarize(res, [n for n, _, _ in sizes], {i: mps[2 * i] for i in range(3)})
-    summ.update({"rate_hz": 120.0, "duration_s": seconds, "launches": st["launches"],
+    summ.update({"rate_hz": 120.0, "duration_s": seconds, "launches": st["launches"] - launches0,
                  "peak_pool_bytes": st["peak_pool_bytes"], "frame_period_ms": 1000.0 / 60.0, "streams": streams,
                  "workload": "Poisson arrivals, 720p/1080p/4K x quarter/macroblock masks, K in {50,100}"})
     return summ

@@ -30,8 +30,9 @@ constexpr int kMaxBatch = 256;   // requests per launch at most
 // class: launched on the high-priority stream of slot 0.
 constexpr long long kShortPixels = 1920ll * 1088ll;
 // S = 32 launches of the server run short-lived CTAs (a warp takes one chunk
-// of blocks), so that the CTAs of a short-class launch are scheduled as soon
-// as CTAs of a running long launch finish.
+// of kShortChunk blocks), so that the CTAs of a short-class launch are
+// scheduled as soon as CTAs of a running long launch finish.
+constexpr int kShortChunk = 4;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -191,8 +192,9 @@ bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt, s->h_tables[slot], tbytes, cudaMemcpyHostToDevice, cs);
     const fsrk::Schedule sc = s->h->sched[s->p.precision][fsri::b_index(s->p.block)];
     if (e == cudaSuccess) {
-        fsrk::BatchArgs a = fsri::batch_args(s->h, dt, n, total, &s->p, sc.chunk);
-        if (s->p.block + 2 * s->p.border == fsrk::S) a.one_round = 1;
+        const bool short_ctas = s->p.block + 2 * s->p.border == fsrk::S;
+        fsrk::BatchArgs a = fsri::batch_args(s->h, dt, n, total, &s->p, short_ctas ? kShortChunk : sc.chunk);
+        a.one_round = short_ctas ? 1 : 0;
         e = fsri::launch_batch(a, &s->p, sc, s->h->sm_count, cs);
     }
     if (e == cudaSuccess) e = cudaEventRecord(L.done, cs);
