@@ -558,7 +558,7 @@ def main():
                        f"{nblocks} blocks x {K_ITERS} iters x 1024 components per launch",
         "fp32": {"achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / fp32_peak,
                  "algorithmic": f"{FLOPS_PER_COMPONENT_ITER} flop per component per iteration"},
-        "kernel": "fsr_batch_kernel<float,4,8,false>",
+        "kernel": "fsr_batch_kernel<float,4,8,false,false>",
         "counters": _counters(smem_peak),
     }
 
