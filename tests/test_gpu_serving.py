@@ -113,3 +113,25 @@ def test_poisson_stream_reports_latencies(fsr_mod, handle):
     s = serving.summarize(res, ["320x180", "160x90"], [0.0576, 0.0144])
     assert s["failed"] == 0 and s["requests"] == arr.size
     assert 0 < s["p50_ms"] <= s["p99_ms"]
+
+
+def test_short_and_long_classes_equal_results_alone(fsr_mod, handle):
+    """Frames above 1920 x 1088 pixels go to the long class (other streams),
+    smaller ones to the high-priority stream; the server's S = 32 launches
+    run short-lived CTAs.  Every result equals the frame reconstructed alone."""
+    fsr = fsr_mod
+    frames = _frames([(1100, 2000, "q"), (90, 130, "mb"), (1090, 1930, "mb"), (57, 75, "q")], seed=21)
+    Ks = [30, 40, 20, 10, 25, 35]
+    with fsr.Server(handle, pool_bytes=256 << 20, max_inflight=8, streams=2) as srv:
+        tickets = {}
+        for j, K in enumerate(Ks):
+            img, mask = frames[j % len(frames)]
+            tickets[srv.submit(img, mask, K)] = (j % len(frames), K)
+        got = {}
+        while len(got) < len(Ks):
+            for t, ms, out in srv.poll(wait_ms=100):
+                assert ms > 0
+                got[t] = out.numpy().copy()
+    for t, (f, K) in tickets.items():
+        img, mask = frames[f]
+        assert np.array_equal(got[t], _alone(fsr, handle, img, mask, K)), (t, K)
