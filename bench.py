@@ -376,7 +376,7 @@ def _measure_batch(fsr, handle, dev, torch):
             "graph": True}
 
 
-def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 2):
+def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 4):
     """Poisson stream, mean 120 req/s: 720p/1080p/4K frames, quarter sampling or
     macroblock loss, K in {50, 100}, through the continuous-batching server."""
     from paper_2202_13926_gb300 import serving, synth
@@ -396,7 +396,7 @@ def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 2):
     iters = rng.choice([50, 100], arr.size)
     with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=streams,
                     block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
-        warm = arr < 1.0   # the first second of the same stream, untimed
+        warm = arr < 2.0   # the first two seconds of the same stream, untimed
         serving.run_stream(srv, frames, arr[warm], kinds[warm], iters[warm])
         launches0 = srv.stats()["launches"]
         res = serving.run_stream(srv, frames, arr, kinds, iters)

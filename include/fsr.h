@@ -243,8 +243,8 @@ int fsr_set_schedule(fsr_handle *h, int block, int precision, const fsr_schedule
  * copies, and launches the admitted, not yet launched requests as batches
  * (fsr_reconstruct_batch's kernel): requests of at most 1920 x 1088 pixels
  * together on the first compute stream, which has the highest stream
- * priority (or on any free stream), larger ones together on the other
- * streams.  Requests that arrive while others run join the next launch, and
+ * priority, larger ones together on the other streams (with one stream,
+ * everything on it).  Requests that arrive while others run join the next launch, and
  * launches, copies in and copies out of different requests overlap on the
  * device.  With S = 32 the server's launches run short-lived CTAs (each warp
  * takes one chunk of blocks), so the blocks of a launch of small

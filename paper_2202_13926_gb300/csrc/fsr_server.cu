@@ -278,8 +278,8 @@ bool step(fsr_server* s) {
         progressed = true;
     }
     // 4. launch the admitted requests (continuous batching): the short class
-    //    on slot 0 (high-priority stream) or any free slot, the long class
-    //    on the other slots
+    //    on slot 0 (high-priority stream), the long class on the other slots
+    //    (one slot: everything on slot 0)
     if (!s->admitted.empty()) {
         std::vector<Request*> shortq, longq;
         for (Request* r : s->admitted) {
@@ -304,7 +304,7 @@ bool step(fsr_server* s) {
         // what is not launched now (no free slot, no room for the table, or
         // beyond kMaxBatch) waits in the admitted list for the next pass
         if (!shortq.empty()) {
-            const int slot = free_slot(true, true);
+            const int slot = free_slot(true, !many);
             if (slot >= 0 && launch_on(s, slot, shortq)) progressed = true;
             s->admitted.insert(s->admitted.end(), shortq.begin(), shortq.end());
         }
