@@ -151,6 +151,11 @@ def _check(code: int, handle) -> None:
 
 def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=True,
                 precision="fp32", seq_out=None, update="single") -> fsr_params:
+    """fsr_params of include/fsr.h: B = block, L = border (support S = B + 2L:
+    32, 24, 16, 8 or 4), K = iters, rho-hat, gamma, w_f switch, precision
+    ("fp32", "fp64", "tc_bf16x3", "tc_tf32"), optional int16 CUDA tensor for
+    the selected indices, update ("single": the paper's; "conj_pair": the
+    ablation of the original FSR's real model)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     upd = UPDATES[update] if isinstance(update, str) else int(update)
     seq_ptr = None
