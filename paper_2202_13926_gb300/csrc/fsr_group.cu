@@ -285,7 +285,9 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     float ar = mu, ai = 0.f;
     float m_lane = (active && Kh > 0) ? split_objective_row<SZ>(zr, zi, wfr, Wd + t * WS, ar, ai) : 0.f;
 
-    for (int nu = 0; nu < Kmax; ++nu) {   // uniform over the warp
+    // One iteration; dc = false when no running group of the warp is in its
+    // DC phase (the split branches then drop out at compile time).
+    auto step = [&](int nu, bool dc) {
         const bool run = active && nu < Kh;
         // a5: block maximum (each group reduces over its own lanes), the
         // lowest row holding it, then its lowest column
@@ -301,7 +303,7 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
         __syncwarp();
         const float2 qv = rowbuf[t];
         float rr = qv.x, ri = qv.y;
-        if (split) {
+        if (dc && split) {
             const float2 w = Wd[u * WS + t];
             split_value(ar, ai, w.x, w.y, qv.x, qv.y, rr, ri);
         }
@@ -323,12 +325,12 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
         }
         // a7 (Eq. 12) and the objective of the next iteration (this group only)
         if (run && nu + 1 < Kh) {
-            if (split && (u | v) == 0) {
+            if (dc && split && (u | v) == 0) {
                 ar -= cr;
                 ai -= ci;
                 m_lane = split_objective_row<SZ>(zr, zi, wfr, Wd + t * WS, ar, ai);
             } else {
-                if (split) {   // fold a W into Q
+                if (dc && split) {   // fold a W into Q
                     const float2* wk = Wd + t * WS;
 #pragma unroll
                     for (int l = 0; l < SZ; ++l) {
@@ -348,7 +350,19 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
                 m_lane = max_all(o2);
             }
         }
+    };
+    // the loops run to the largest K of the warp (uniform).  S = 4, 8: a DC
+    // loop, then a loop without the split branches (S = 4 0.385 -> 0.365 ms,
+    // S = 8 0.776 -> 0.747 ms per 1080p frame); S = 16 keeps one loop (two
+    // copies of its larger body measured 2.07 -> 2.15 ms).
+    if constexpr (SZ < 16) {
+        int nu = 0;
+        while (nu < Kmax && __any_sync(FULL, split && active && nu < Kh)) step(nu++, true);
+        for (; nu < Kmax; ++nu) step(nu, false);
+    } else {
+        for (int nu = 0; nu < Kmax; ++nu) step(nu, true);
     }
+
 
     // ---- a9: write-back of the B x B target ----
 #pragma unroll
