@@ -394,12 +394,32 @@ def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 4):
     rng = np.random.default_rng(10)
     kinds = rng.integers(0, len(frames), arr.size)
     iters = rng.choice([50, 100], arr.size)
+    class _Outputs:   # output buffers reused like a serving client's (no pinned allocation while timed)
+        def __init__(self, srv, shapes, n=24):
+            self.srv, self.shape_of = srv, {}
+            self.free = {sh: [torch.empty(sh, dtype=torch.float32).pin_memory() for _ in range(n)] for sh in shapes}
+
+        def submit(self, a, b, k):
+            key = tuple(a.shape)
+            pool = self.free.setdefault(key, [])
+            out = pool.pop() if pool else torch.empty(key, dtype=torch.float32).pin_memory()
+            t = self.srv.submit(a, b, k, out=out)
+            self.shape_of[t] = key
+            return t
+
+        def poll(self, wait_ms=0):
+            done = self.srv.poll(wait_ms)
+            for t, _ms, out in done:
+                self.free[self.shape_of.pop(t)].append(out)
+            return done
+
     with fsr.Server(handle, pool_bytes=3 << 30, max_inflight=64, streams=streams,
                     block=B, border=L, rho=RHO, gamma=GAMMA) as srv:
+        client = _Outputs(srv, {tuple(f[0].shape) for f in frames})
         warm = arr < 2.0   # the first two seconds of the same stream, untimed
-        serving.run_stream(srv, frames, arr[warm], kinds[warm], iters[warm])
+        serving.run_stream(client, frames, arr[warm], kinds[warm], iters[warm])
         launches0 = srv.stats()["launches"]
-        res = serving.run_stream(srv, frames, arr, kinds, iters)
+        res = serving.run_stream(client, frames, arr, kinds, iters)
         st = srv.stats()
     res["kinds"] = np.asarray([cls[k] for k in kinds])
     summ = serving.summarize(res, [n for n, _, _ in sizes], {i: mps[2 * i] for i in range(3)})

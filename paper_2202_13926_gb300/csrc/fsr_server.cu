@@ -29,9 +29,10 @@ constexpr int kMaxBatch = 256;   // requests per launch at most
 // Requests of at most this many pixels (1080p and smaller) are the short
 // class: launched on the high-priority stream of slot 0.
 constexpr long long kShortPixels = 1920ll * 1088ll;
-// S = 32 launches of the server run short-lived CTAs (a warp takes one chunk
-// of kShortChunk blocks), so that the CTAs of a short-class launch are
-// scheduled as soon as CTAs of a running long launch finish.
+// S = 32 launches of the long class run short-lived CTAs (a warp takes one
+// chunk of kShortChunk blocks), so that the CTAs of a short-class launch
+// (persistent, high priority) are scheduled as soon as CTAs of a running
+// long launch finish.
 constexpr int kShortChunk = 4;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -161,7 +162,7 @@ void finish(fsr_server* s, Request* r, Clock::time_point now) {
 // Launches up to kMaxBatch of the requests in q (taken from its front) as
 // one batch on the given free slot; the rest stay in q.  Returns false when
 // the launch table does not fit in the pool now (nothing launched).
-bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q) {
+bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q, bool long_class) {
     const int n = (int)std::min<size_t>(q.size(), kMaxBatch);
     Launch& L = s->launches[slot];
     size_t toff = 0;
@@ -192,7 +193,7 @@ bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt, s->h_tables[slot], tbytes, cudaMemcpyHostToDevice, cs);
     const fsrk::Schedule sc = s->h->sched[s->p.precision][fsri::b_index(s->p.block)];
     if (e == cudaSuccess) {
-        const bool short_ctas = s->p.block + 2 * s->p.border == fsrk::S;
+        const bool short_ctas = long_class && s->p.block + 2 * s->p.border == fsrk::S;
         fsrk::BatchArgs a = fsri::batch_args(s->h, dt, n, total, &s->p, short_ctas ? kShortChunk : sc.chunk);
         a.one_round = short_ctas ? 1 : 0;
         e = fsri::launch_batch(a, &s->p, sc, s->h->sm_count, cs);
@@ -305,12 +306,12 @@ bool step(fsr_server* s) {
         // beyond kMaxBatch) waits in the admitted list for the next pass
         if (!shortq.empty()) {
             const int slot = free_slot(true, !many);
-            if (slot >= 0 && launch_on(s, slot, shortq)) progressed = true;
+            if (slot >= 0 && launch_on(s, slot, shortq, false)) progressed = true;
             s->admitted.insert(s->admitted.end(), shortq.begin(), shortq.end());
         }
         if (!longq.empty()) {
             const int slot = free_slot(!many, many);
-            if (slot >= 0 && launch_on(s, slot, longq)) progressed = true;
+            if (slot >= 0 && launch_on(s, slot, longq, true)) progressed = true;
             s->admitted.insert(s->admitted.end(), longq.begin(), longq.end());
         }
     }
