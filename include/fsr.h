@@ -123,7 +123,8 @@ const char *fsr_last_error(const fsr_handle *h);
  *          enqueues work and returns.
  * Errors: INVALID_ARG (NULL pointers, sizes <= 0, pitch < width, overlap,
  * parameters out of range), UNSUPPORTED (a support or block size not listed at
- * fsr_params.border, a tensor-core mode with S < 32),
+ * fsr_params.border, a tensor-core mode with S < 32, FSR_UPDATE_CONJ_PAIR
+ * outside S = 32, B = 4, FSR_FP32 / FSR_FP64_DEBUG),
  * CUDA (launch failure). */
 int fsr_reconstruct(fsr_handle *h, const float *img, const uint8_t *mask,
                     int height, int width, int pitch, const fsr_params *p,
