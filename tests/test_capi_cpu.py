@@ -67,3 +67,20 @@ def test_status_entry_points_reject_null_handle(lib):
     assert lib.fsr_inject_tile_wait_fault(None) == fsr.FSR_ERR_INVALID_ARG
     c = ctypes.c_longlong()
     assert lib.fsr_empty_blocks(None, None, ctypes.byref(c)) == fsr.FSR_ERR_INVALID_ARG
+
+
+def test_static_batch_rejects_bad_parameters_before_any_device_work(lib):
+    """The allocation-free batch entry point validates its parameters on the
+    host first: these calls return their codes without touching a GPU."""
+    d = (fsr.fsr_image_desc * 1)(fsr.fsr_image_desc(1, 1, 1, 8, 8, 8, 10, None))
+    buf = ctypes.create_string_buffer(256)
+    cases = [(fsr.make_params(update="conj_pair"), fsr.FSR_ERR_UNSUPPORTED),
+             (fsr.make_params(block=4, border=6), fsr.FSR_ERR_UNSUPPORTED),
+             (fsr.make_params(precision="tc_bf16x3"), fsr.FSR_ERR_UNSUPPORTED),
+             (fsr.make_params(rho=0.0), fsr.FSR_ERR_INVALID_ARG)]
+    for p, code in cases:
+        got = lib.fsr_reconstruct_batch_static(1, d, ctypes.byref(p), None, buf, len(buf))
+        assert got == code, (got, buf.value)
+        assert buf.value
+    assert lib.fsr_reconstruct_batch_static(0, d, ctypes.byref(fsr.make_params()), None, buf,
+                                            len(buf)) == fsr.FSR_ERR_INVALID_ARG
