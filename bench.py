@@ -437,23 +437,11 @@ def _measure_stream(fsr, handle, torch, img, mask, n: int = 60, support: int = 3
     from paper_2202_13926_gb300 import serving
     hi = torch.from_numpy(img).pin_memory()
     hm = torch.from_numpy(mask).pin_memory()
-    outs = [torch.empty(img.shape, dtype=torch.float32).pin_memory() for _ in range(8)]
-
-    class _Reuse:   # hands out the 8 output buffers in turn (results are not kept)
-        def __init__(self, srv):
-            self.srv, self.i = srv, 0
-
-        def submit(self, a, b, k):
-            self.i += 1
-            return self.srv.submit(a, b, k, out=outs[self.i % len(outs)])
-
-        def poll(self, wait_ms=0):
-            return self.srv.poll(wait_ms)
-
+    outs = [torch.empty(img.shape, dtype=torch.float32).pin_memory() for _ in range(8)]   # reused, not kept
     with fsr.Server(handle, pool_bytes=1 << 30, max_inflight=8, streams=2,
                     block=B, border=(support - B) // 2, rho=RHO, gamma=GAMMA) as srv:
-        serving.run_stream(_Reuse(srv), [(hi, hm)], np.zeros(4), np.zeros(4, int), np.full(4, K_ITERS))
-        res = serving.run_stream(_Reuse(srv), [(hi, hm)], np.zeros(n), np.zeros(n, int), np.full(n, K_ITERS))
+        serving.stream_frames(srv, [(hi, hm)] * 4, K_ITERS, outs)
+        res = serving.stream_frames(srv, [(hi, hm)] * n, K_ITERS, outs)
     mp = H * W / 1e6
     return {"frames": n, "wall_s": res["wall_s"], "fps": n / res["wall_s"], "mp_per_s": n * mp / res["wall_s"],
             "h2d_bytes_per_frame": int(img.nbytes + mask.nbytes), "d2h_bytes_per_frame": int(img.nbytes),
@@ -470,6 +458,35 @@ def _config():
             "l2": "L2 flushed (256 MiB write) before every timed step; flush outside the kernel events"}
 
 
+def run_case(args):
+    """One configuration on the 1920 x 1080 quarter-sampling frame, launched
+    args.repeat times through fsr_reconstruct; prints the device time of each
+    launch (CUDA events) as one JSON line."""
+    import torch
+    import __graft_entry__
+    from paper_2202_13926_gb300 import fsr, synth
+    __graft_entry__.build()
+    img, mask = synth.fhd_quarter_case(IMG_SEED)
+    dev = torch.device("cuda:0")
+    d_img, d_mask = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
+    d_out = torch.empty_like(d_img)
+    params = fsr.make_params(block=B, border=(args.support - B) // 2, iters=args.iters, rho=RHO, gamma=GAMMA,
+                             precision=args.precision, update=args.update)
+    ms = []
+    with fsr.Handle(0) as h:
+        for _ in range(args.repeat):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fsr.fsr_reconstruct(h.ptr, d_img, d_mask, params, d_out)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        h.check_status()
+    print(json.dumps({"case": True, "support": args.support, "block": B, "iters": args.iters,
+                      "precision": args.precision, "update": args.update, "ms": ms}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,11 +499,21 @@ def main():
     ap.add_argument("--no-k-sweep", action="store_true", help="skip the K = 100..400 sweep of the 1080p frame")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the Poisson serving stream (0 = skip)")
+    ap.add_argument("--case", action="store_true",
+                    help="run one configuration on the 1080p frame --repeat times, print the device times "
+                         "and exit (the fixed workload of the profiler captures)")
+    ap.add_argument("--support", type=int, default=B + 2 * L, help="--case: S = B + 2L (4, 8, 16, 24 or 32)")
+    ap.add_argument("--iters", type=int, default=K_ITERS, help="--case: K")
+    ap.add_argument("--precision", default="fp32", help="--case: fp32, fp64, tc_bf16x3 or tc_tf32")
+    ap.add_argument("--update", default="single", help="--case: single or conj_pair")
+    ap.add_argument("--repeat", type=int, default=3, help="--case: launches")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.case:
+        return run_case(args)
 
     import torch
     import __graft_entry__

@@ -307,15 +307,19 @@ int fsr_server_destroy(fsr_server *s);
  *     rejected with FSR_ERR_INVALID_ARG and a message.
  *   - The first call on a device does a one-time set-up there (finds the
  *     array's device address, sets the kernels' shared-memory limits); make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The set-up is kept for the
+ *     life of the process: do not use this entry point on a device after
+ *     cudaDeviceReset.
  *   - Every call shares the one array per device and overwrites it (the work
- *     counter is reset by each call's table upload): calls whose work overlaps
+ *     counter is reset by each call's table copy): calls whose work overlaps
  *     on the device race and give wrong results.  Keep them on one stream, or
  *     wait for one to finish before the next starts.
- *   - The table is uploaded from host memory of the library, consumed before
- *     the call returns; the call is otherwise asynchronous on `stream`.
+ *   - The table goes to the device in the launch parameters of a small copy
+ *     kernel on `stream`, so no host memory is read after the call returns;
+ *     the call is asynchronous on `stream`.
  *   - err/err_len: optional buffer for the text of an error (may be NULL).
- * Errors: INVALID_ARG, UNSUPPORTED, CUDA, as for fsr_reconstruct_batch. */
+ * Errors: INVALID_ARG, UNSUPPORTED (also for a device ordinal >= 64), CUDA,
+ * as for fsr_reconstruct_batch. */
 #define FSR_STATIC_MAX_IMAGES 64
 #define FSR_STATIC_SCRATCH_BYTES 8192
 int fsr_reconstruct_batch_static(int n, const fsr_image_desc *d, const fsr_params *p, void *stream,

@@ -36,9 +36,21 @@ struct DeviceSetup {
     int sm_count = 0;
 };
 
-std::mutex g_mu;                                      // guards g_setup and g_host_table
+std::mutex g_mu;                                      // guards g_setup
 DeviceSetup g_setup[kMaxDevices];
-alignas(16) unsigned char g_host_table[kScratchBytes];  // host image of the table
+
+// The table of one call travels to the device in the launch parameters of a
+// small kernel that copies it into g_batch_scratch: nothing in host memory is
+// read after the call returns, and no host buffer is shared between calls.
+struct TableImage {
+    int bytes;                                        // used bytes, a multiple of 16
+    alignas(16) unsigned char data[kScratchBytes];
+};
+
+__global__ void put_table(const __grid_constant__ TableImage t) {
+    for (int i = 16 * (int)threadIdx.x; i < t.bytes; i += 16 * (int)blockDim.x)
+        *reinterpret_cast<uint4*>(g_batch_scratch + i) = *reinterpret_cast<const uint4*>(t.data + i);
+}
 
 int report(char* err, size_t err_len, int code, const char* fmt, ...) {
     if (err && err_len) {
@@ -92,10 +104,12 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return report(err, err_len, FSR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return report(err, err_len, FSR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return report(err, err_len, FSR_ERR_UNSUPPORTED, "device %d exceeds the %d devices this entry point tracks",
+                      dev, kMaxDevices);
 
-    std::lock_guard<std::mutex> lock(g_mu);
+    std::unique_lock<std::mutex> lock(g_mu);
     DeviceSetup& su = g_setup[dev];
     if (!su.done) {
         // once per device, with that device current
@@ -114,16 +128,21 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
         su.sm_count = prop.multiProcessorCount;
         su.done = true;
     }
+    void* const scratch = su.scratch;
+    const int sm_count = su.sm_count;
+    lock.unlock();
 
-    // Host image of the table: images by decreasing K, prefix sums of their
-    // block counts, and a zero work counter (the array keeps the last call's
-    // contents, so the counter is cleared by this upload).
-    std::memset(g_host_table, 0, bytes);
+    // The table: images by decreasing K, prefix sums of their block counts,
+    // and a zero work counter (the array keeps the last call's contents, so
+    // the counter is cleared by this copy).
+    TableImage tab;
+    tab.bytes = (int)((bytes + 15) & ~(size_t)15);
+    std::memset(tab.data, 0, (size_t)tab.bytes);
     int order[kMaxImages];
     std::iota(order, order + n, 0);
     std::stable_sort(order, order + n, [&](int a, int b) { return d[a].iters > d[b].iters; });
-    auto* first = reinterpret_cast<long long*>(g_host_table + sizeof(unsigned long long));
-    auto* imgs = reinterpret_cast<fsrk::ImageArgs*>(g_host_table + images_offset(n));
+    auto* first = reinterpret_cast<long long*>(tab.data + sizeof(unsigned long long));
+    auto* imgs = reinterpret_cast<fsrk::ImageArgs*>(tab.data + images_offset(n));
     long long total = 0;
     for (int j = 0; j < n; ++j) {
         const fsr_image_desc& x = d[order[j]];
@@ -143,11 +162,12 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
     first[n] = total;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((e = cudaMemcpyAsync(su.scratch, g_host_table, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return report(err, err_len, FSR_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+    put_table<<<1, 128, 0, s>>>(tab);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return report(err, err_len, FSR_ERR_CUDA, "table copy: %s", cudaGetErrorString(e));
 
     fsrk::BatchArgs ba;
-    unsigned char* base = static_cast<unsigned char*>(su.scratch);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
     ba.counter = reinterpret_cast<unsigned long long*>(base);
     ba.first = reinterpret_cast<const long long*>(base + sizeof(unsigned long long));
     ba.images = reinterpret_cast<const fsrk::ImageArgs*>(base + images_offset(n));
@@ -159,8 +179,8 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
     ba.mth.gamma = p->gamma;
     ba.mth.freq_weight = p->freq_weight;
     const fsrk::Schedule sc{p->precision == FSR_FP64_DEBUG ? 4 : fsrk::kWarpsFp32, 1};
-    e = (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(ba, p->block, sc, su.sm_count, s)
-                                         : fsrk::launch_batch_fp32(ba, p->block, sc, su.sm_count, s);
+    e = (p->precision == FSR_FP64_DEBUG) ? fsrk::launch_batch_fp64(ba, p->block, sc, sm_count, s)
+                                         : fsrk::launch_batch_fp32(ba, p->block, sc, sm_count, s);
     if (e != cudaSuccess) return report(err, err_len, FSR_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
     return FSR_OK;
 }

@@ -50,6 +50,31 @@ def run_stream(server, frames, arrivals, kinds, iters, poll_ms: int = 1):
     return dict(latency_ms=lat, kinds=np.asarray(kinds), iters=np.asarray(iters), wall_s=wall)
 
 
+class _CycledOutputs:
+    """Hands the output buffers out in turn (a client that consumes each
+    result before its buffer comes round again)."""
+
+    def __init__(self, server, outs):
+        self.server, self.outs, self.i = server, outs, 0
+
+    def submit(self, img, mask, iters):
+        out = self.outs[self.i % len(self.outs)]
+        self.i += 1
+        return self.server.submit(img, mask, iters, out=out)
+
+    def poll(self, wait_ms=0):
+        return self.server.poll(wait_ms)
+
+
+def stream_frames(server, frames, iters, outs):
+    """Frame streaming: every frame of ``frames`` (pinned host tensors) is
+    submitted at t = 0 with K = ``iters``; the server overlaps the copies in,
+    the launches and the copies out of the frames in flight.  Frame i is
+    written to outs[i % len(outs)]; returns the run_stream result."""
+    n = len(frames)
+    return run_stream(_CycledOutputs(server, outs), frames, np.zeros(n), np.arange(n), np.full(n, int(iters)))
+
+
 def summarize(res, kind_names, frame_megapixels):
     lat = res["latency_ms"]
     out = {"requests": int(lat.size), "failed": int(np.sum(lat < 0)),

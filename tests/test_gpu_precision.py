@@ -107,6 +107,17 @@ def test_precision_study_on_1080p_quarter_sampling(handle):
         with open(out, "w") as fh:
             json.dump(rows, fh, indent=1)
     assert rows["fp32"]["frac_within_0.5"] >= PA.FRAC_MIN
-    # the split-product transform keeps ~16 bits; TF32 ~11: both must stay usable
-    assert abs(rows["tc_bf16x3"]["dpsnr_db"]) <= 0.1
-    assert abs(rows["tc_tf32"]["dpsnr_db"]) <= 1.0
+    # Every mode meets the PSNR part of the acceptance bar.  The share of
+    # pixels within 0.5 grey levels depends on the transform's precision: the
+    # hi/lo split carries 16 significant bits of each operand (two 8-bit BF16
+    # mantissas), TF32 11, against FP32's 24, so near-ties of the greedy
+    # selection flip more often; the floors below sit a little under the
+    # measured shares (BF16x3 0.9937, TF32 0.7407), and the RMS difference at
+    # the unknown pixels is bounded per mode a little above the measured
+    # values (FP32 0.026, BF16x3 0.120, TF32 0.817 grey levels), so a
+    # regression in either tensor-core transform fails here.
+    floors = {"fp32": (PA.FRAC_MIN, 0.05), "tc_bf16x3": (0.990, 0.2), "tc_tf32": (0.70, 1.0)}
+    for mode, (frac_min, rms_max) in floors.items():
+        assert abs(rows[mode]["dpsnr_db"]) <= PA.PSNR_TOL_DB, mode
+        assert rows[mode]["frac_within_0.5"] >= frac_min, mode
+        assert rows[mode]["rms_vs_oracle_unknown"] <= rms_max, mode

@@ -63,6 +63,31 @@ def test_fp32_matches_the_oracle(handle, S, B):
     assert dpsnr <= PA.PSNR_TOL_DB, (S, B, dpsnr)
 
 
+@pytest.mark.parametrize("S", [4, 8, 16, 24])
+def test_fp32_full_1080p_frame_matches_the_oracle(handle, S):
+    """The whole 1920 x 1080 quarter-sampling frame at K = 100, B = 4, in the
+    launch configuration of the support-size sweep, against the oracle on
+    every block.  The frame has far more blocks than the grid has resident
+    warps (at most 64 warps per SM; the group kernel puts 32 / S blocks on a
+    warp), so every warp runs its work loop many times: the per-block state
+    reset and the tile-buffer parity flip between blocks are compared with
+    the oracle here, not only the first block of each warp."""
+    img, mask = synth.fhd_quarter_case()
+    B = 4
+    nblocks = -(-img.shape[0] // B) * -(-img.shape[1] // B)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks_per_warp = 32 // S if S in (4, 8, 16) else 1
+    assert nblocks > 64 * sms * blocks_per_warp, (nblocks, sms)
+    got = _run(handle, img, mask, S, B, 100)
+    ref, _ = _oracle(img, mask, S, B, 100)
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    frac = PA.frac_within(got, ref)
+    dpsnr = abs(PA.psnr(got, img) - PA.psnr(ref, img))
+    print(f"S = {S}: within 0.5 {frac:.5f}, dPSNR {dpsnr:.2e} dB")
+    assert frac >= PA.FRAC_MIN, (S, frac)
+    assert dpsnr <= PA.PSNR_TOL_DB, (S, dpsnr)
+
+
 @pytest.mark.parametrize("S,B", CASES)
 def test_fp64_selection_sequences(handle, S, B):
     img, mask = synth.small_case(seed=4)
@@ -135,7 +160,7 @@ def test_fp32_batch_of_ragged_images_with_mixed_K(fsr_mod, handle, S, B):
     every image equals its single-image call bit for bit, and the oracle."""
     fsr = fsr_mod
     dev = torch.device("cuda:0")
-    specs = [((17, 17), 40), ((1, 1), 13), ((37, 21), 0), ((13, 17), 25)]
+    specs = [((67, 75), 40), ((1, 1), 13), ((37, 21), 0), ((53, 71), 25)]
     items = []
     for i, ((H, W), K) in enumerate(specs):
         img = synth.sinusoid_image(H, W, seed=90 + i)
@@ -153,4 +178,8 @@ def test_fp32_batch_of_ragged_images_with_mixed_K(fsr_mod, handle, S, B):
         ref, _ = _oracle(img, mk, S, B, K)
         gots.append(got.ravel())
         refs.append(ref.ravel())
-    assert PA.frac_within(np.concatenate(gots), np.concatenate(refs)) >= 0.99
+    # the acceptance share of tests/parity.py, at least one pixel on these
+    # few thousand pixels (as for the ragged sizes of the S = 32 tests)
+    got_all, ref_all = np.concatenate(gots), np.concatenate(refs)
+    n_out = int(np.sum(np.abs(got_all - ref_all) > PA.GREY_TOL))
+    assert n_out <= max(1, int((1 - PA.FRAC_MIN) * got_all.size)), (S, B, n_out, got_all.size)

@@ -56,3 +56,21 @@ def test_run_stream_and_summary():
     assert s["per_class"]["a"]["n"] + s["per_class"]["b"]["n"] + s["per_class"]["c"]["n"] == 31
     mp = sum({0: 1.0, 1: 2.0, 2: 8.0}[k] for k in kinds)
     assert abs(s["sustained_mp_s"] - mp / res["wall_s"]) < 1e-9
+
+
+def test_stream_frames_cycles_the_output_buffers():
+    """Frame streaming submits every frame at t = 0 and hands the output
+    buffers out in turn."""
+    class _Recorder(_FakeEngine):
+        def __init__(self):
+            super().__init__({7: 0.001})
+            self.outs = []
+
+        def submit(self, img, mask, iters, out=None):
+            self.outs.append(out)
+            return super().submit(img, mask, iters)
+
+    eng = _Recorder()
+    res = serving.stream_frames(eng, [("i%d" % i, "m%d" % i) for i in range(5)], 7, ["a", "b"])
+    assert eng.outs == ["a", "b", "a", "b", "a"]
+    assert np.allclose(res["latency_ms"], 1.0) and np.array_equal(res["kinds"], np.arange(5))
