@@ -565,15 +565,18 @@ __device__ __forceinline__ unsigned load_support(const ImageArgs& a, int y0, int
     return known;
 }
 
-// a1-a3: load the support (lane n = column n), weight it, transform it.
-// On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
-// row k in zr/zi and the W rows are in Wd (layout of WRow<T>).
-template <typename T, int WS, Dft DFT>
-__device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
-                                              const T* __restrict__ sw0,
-                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
-                                              const unsigned char* tile,
-                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
+// a1-a3 up to the packed spectrum: load the support (lane n = column n),
+// weight it and transform z = x + j alpha w.  On return (when some pixel is
+// known) lane k holds Z[k][0..31] = F2{z} row k in zr/zi; inv2alpha =
+// 1 / (2 alpha); swd: sum of w in FP64 (precision study only).  Wd: this
+// warp's scratch (the support tile and the transpose pass through it).
+template <typename T, Dft DFT>
+__device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int x0, int lane,
+                                                const T* __restrict__ sw0,
+                                                typename Vec2<T>::type* Wd, const unsigned char* tctab,
+                                                const unsigned char* tile,
+                                                T (&zr)[S], T (&zi)[S], BlockState<T>& st, T& inv2alpha_out,
+                                                double& swd_out) {
     using T2 = typename Vec2<T>::type;
     const unsigned known = load_support<T>(a, y0, x0, lane, tile, zr);
     T sw = T(0), sfw = T(0);
@@ -641,6 +644,24 @@ __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0
         // FFT over n: lane k holds Z[k][0..31]
         fft32<T>(zr, zi);
     }
+    inv2alpha_out = inv2alpha;
+    swd_out = swd;
+    return true;
+}
+
+// a1-a3: load the support (lane n = column n), weight it, transform it.
+// On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
+// row k in zr/zi and the W rows are in Wd (layout of WRow<T>).
+template <typename T, int WS, Dft DFT>
+__device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
+                                              const T* __restrict__ sw0,
+                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
+                                              const unsigned char* tile,
+                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
+    using T2 = typename Vec2<T>::type;
+    T inv2alpha;
+    double swd;
+    if (!transform_block<T, DFT>(a, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st, inv2alpha, swd)) return false;
 
     // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,  W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha)
     const int src = (S - lane) & (S - 1);
