@@ -10,6 +10,7 @@ from .oracle import (  # noqa: F401
     dft2_real,
     fsr_block,
     fsr_image_blocks,
+    fsr_image_reuse,
     assemble_image,
     max_threads,
     default,

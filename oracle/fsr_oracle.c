@@ -127,11 +127,15 @@ void fsr_oracle_dft2_real(int S, const double *x, double *Xre, double *Xim)
     free(Tre); free(Tim); free(Yre); free(Yim);
 }
 
-/* One support block: Eqs. (2), (5)-(12) in order. */
-int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
-                     const unsigned char *known, fsr_oracle_block_out *o)
+/* One support block: Eqs. (2), (5)-(12) in order.  scale[i] multiplies the
+ * weight of Eq. (5) at pixel i: 1 on the known set K of Eq. (2), 0 on
+ * unknown pixels, and in the re-use form of fsr_oracle_image_reuse the
+ * re-use weight delta on pixels reconstructed by earlier blocks (reading:
+ * those pixels join the set of Eq. 2 with the weight delta rho^dist). */
+int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
+                            const double *scale, fsr_oracle_block_out *o)
 {
-    if (!P || !f || !known || P->S <= 0 || P->K < 0) return -1;
+    if (!P || !f || !scale || P->S <= 0 || P->K < 0) return -1;
     const int S = P->S, K = P->K, SS = S * S;
     int skipped = 0;
 
@@ -148,11 +152,11 @@ int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
         for (int i = 0; i < SS; ++i) wf[i] = 1.0;
     }
 
-    /* Eqs. (2), (5), (6): w = w0 on known pixels, 0 elsewhere; the weighted
-     * sampled signal f~ . w.  Unknown values are never read. */
+    /* Eqs. (2), (5), (6): w = w0 on known pixels (scale 1), 0 elsewhere;
+     * the weighted sampled signal f~ . w.  Unknown values are never read. */
     for (int i = 0; i < SS; ++i) {
-        w[i] = known[i] ? w0[i] : 0.0;
-        x[i] = known[i] ? f[i] * w[i] : 0.0;
+        w[i] = scale[i] > 0.0 ? scale[i] * w0[i] : 0.0;
+        x[i] = scale[i] > 0.0 ? f[i] * w[i] : 0.0;
     }
     /* Eq. (7) and the weighting spectrum W = F2{w}. */
     fsr_oracle_dft2_real(S, x, Rre, Rim);
@@ -170,7 +174,7 @@ int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
     /* Reading: a block without a known pixel has W[0,0] = 0 and Eq. (10) is
      * undefined; the model stays G = 0. */
     int any_known = 0;
-    for (int i = 0; i < SS; ++i) any_known |= (known[i] != 0);
+    for (int i = 0; i < SS; ++i) any_known |= (scale[i] > 0.0);
     if (!any_known) skipped = 1;
 
     for (int nu = 0; nu < K; ++nu) {
@@ -322,6 +326,19 @@ int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
     return skipped;
 }
 
+/* The paper's block routine: weight w0 on the known set, 0 elsewhere. */
+int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
+                     const unsigned char *known, fsr_oracle_block_out *o)
+{
+    if (!P || !f || !known || P->S <= 0 || P->K < 0) return -1;
+    const int SS = P->S * P->S;
+    double *scale = malloc(sizeof(double) * SS);
+    for (int i = 0; i < SS; ++i) scale[i] = known[i] ? 1.0 : 0.0;
+    int r = fsr_oracle_block_scaled(P, f, scale, o);
+    free(scale);
+    return r;
+}
+
 int fsr_oracle_max_threads(void)
 {
 #ifdef _OPENMP
@@ -397,5 +414,83 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
             }
         free(f); free(kn); free(gre); free(gim); free(need);
     }
+    return bad ? -1 : n_empty;
+}
+
+/* Re-use of reconstructed pixels: the sequential form of the original FSR,
+ * which the paper leaves out in Sec. II for the sake of parallelism.
+ * Readings (the paper does not define this form):
+ *   - blocks are processed one after the other in line-scan (raster) order
+ *     b = by*nbx + bx;
+ *   - when block b runs, an unknown pixel of the target of an earlier block
+ *     (b' < b) holds that block's reconstruction Re g and takes part in the
+ *     support of b with the weight delta rho^dist (delta: the re-use weight);
+ *     unknown pixels of later blocks stay unknown;
+ *   - everything else is the paper's block routine; delta = 0 gives the
+ *     independent blocks of fsr_oracle_image_blocks.
+ * out: H x Wd (row pitch Wd) reconstruction of blocks 0 .. nblocks-1 (known
+ * pixels copied, NaN on pixels of later blocks); nblocks <= 0: all blocks.
+ * seq, margin: optional nblocks*K.  Single-threaded (each block depends on
+ * the ones before it).  Returns the number of blocks without any known or
+ * re-used pixel, or -1 on error. */
+long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
+                            int H, int Wd, int pitch, int B, int L,
+                            const fsr_oracle_params *P, double delta, long nblocks,
+                            double *out, int *seq, double *margin)
+{
+    if (!img || !mask || !P || !out || H <= 0 || Wd <= 0 || pitch < Wd ||
+        B <= 0 || L < 0 || P->S != B + 2 * L || P->K < 0 || !(delta >= 0.0 && delta <= 1.0))
+        return -1;
+    const int S = P->S, K = P->K;
+    const long nbx = (Wd + B - 1) / B, nby = (H + B - 1) / B;
+    if (nblocks <= 0 || nblocks > nbx * nby) nblocks = nbx * nby;
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < Wd; ++x)
+            out[y * Wd + x] = mask[y * pitch + x] ? (double)img[y * pitch + x] : NAN;
+    double *f = malloc(sizeof(double) * S * S), *scale = malloc(sizeof(double) * S * S);
+    double *gre = malloc(sizeof(double) * S * S);
+    unsigned char *need = calloc((size_t)S * S, 1);
+    for (int a = 0; a < B; ++a)
+        for (int c = 0; c < B; ++c) need[(L + a) * S + (L + c)] = 1;
+    long n_empty = 0;
+    int bad = 0;
+    for (long b = 0; b < nblocks && !bad; ++b) {
+        const long by = b / nbx;          /* raster order: block row, then column */
+        const long bx = b - by * nbx;
+        const long y0 = by * B - L;       /* support origin (Sec. III-A) */
+        const long x0 = bx * B - L;
+        for (int m = 0; m < S; ++m)
+            for (int n = 0; n < S; ++n) {
+                const long y = y0 + m, x = x0 + n;
+                double v = 0.0, sc = 0.0;
+                if (y >= 0 && y < H && x >= 0 && x < Wd) {      /* reading: outside = unknown */
+                    if (mask[y * pitch + x]) {
+                        v = (double)img[y * pitch + x];
+                        sc = 1.0;
+                    } else if ((y / B) * nbx + (x / B) < b) {    /* reconstructed by an earlier block */
+                        v = out[y * Wd + x];
+                        sc = delta;
+                    }
+                }
+                f[m * S + n] = v;
+                scale[m * S + n] = sc;
+            }
+        fsr_oracle_block_out o;
+        memset(&o, 0, sizeof o);
+        o.seq = seq ? seq + b * K : NULL;
+        o.margin = margin ? margin + b * K : NULL;
+        o.gre = gre;
+        o.g_need = need;
+        int r = fsr_oracle_block_scaled(P, f, scale, &o);
+        if (r < 0) bad = 1;
+        if (r == 1) n_empty += 1;
+        /* write-back of the target: unknown pixels take Re g */
+        for (int a = 0; a < B; ++a)
+            for (int c = 0; c < B; ++c) {
+                const long y = y0 + L + a, x = x0 + L + c;
+                if (y < H && x < Wd && !mask[y * pitch + x]) out[y * Wd + x] = gre[(L + a) * S + (L + c)];
+            }
+    }
+    free(f); free(scale); free(gre); free(need);
     return bad ? -1 : n_empty;
 }

@@ -70,6 +70,12 @@ void fsr_oracle_dft2_real(int S, const double *x, double *Xre, double *Xim);
 int fsr_oracle_block(const fsr_oracle_params *P, const double *f,
                      const unsigned char *known, fsr_oracle_block_out *o);
 
+/* The block routine with a weight scale per pixel: w = scale * w0 (Eq. 5),
+ * pixels with scale 0 are unknown (the set K of Eq. 2 is {scale > 0}).
+ * fsr_oracle_block is this routine with scale = 1 on known pixels, 0 else. */
+int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
+                            const double *scale, fsr_oracle_block_out *o);
+
 /* FSR over selected blocks of an image (Sec. III-A tiling).
  * img/mask: H x Wd, row pitch in elements; mask nonzero = known.
  * Block b = by * nbx + bx with nbx = ceil(Wd/B), nby = ceil(H/B).
@@ -85,6 +91,18 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                              const fsr_oracle_params *P, long nsel,
                              const long *block_ids, int nthreads,
                              double *out_target, double *out_im, int *seq, double *margin);
+
+/* Re-use of reconstructed pixels (the sequential form the paper leaves out,
+ * Sec. II): blocks in raster order; unknown pixels of earlier blocks' targets
+ * enter later supports with their reconstruction and the weight
+ * delta * rho^dist.  out: H x Wd reconstruction of the first nblocks blocks
+ * (<= 0: all; NaN on unknown pixels of later blocks); seq, margin optional
+ * (nblocks*K).  Returns the number of blocks without any known or re-used
+ * pixel, or -1 on error. */
+long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
+                            int H, int Wd, int pitch, int B, int L,
+                            const fsr_oracle_params *P, double delta, long nblocks,
+                            double *out, int *seq, double *margin);
 
 /* Number of OpenMP threads the image routine would use by default. */
 int fsr_oracle_max_threads(void);

@@ -7,6 +7,9 @@ Each wrapper names the part of the paper its C routine follows:
   dft2_real       the 2-D DFT F2 of Eq. (7)
   fsr_block       Sec. II, Eqs. (2), (5)-(12) on one support block
   fsr_image_blocks Sec. III-A tiling, Eq. (13), plus the write-back of Sec. II
+  fsr_image_reuse the sequential form that re-uses reconstructed pixels, which
+                  Sec. II leaves out (blocks in raster order; reading stated in
+                  fsr_oracle.c)
 With ``conj_pairs`` the two block routines run the ablation of the original
 FSR's real model (the selected component and its conjugate updated together),
 which is not the paper's Eqs. (11)-(12).
@@ -78,6 +81,13 @@ class OracleLib:
                                          ctypes.POINTER(ctypes.c_ubyte),
                                          ctypes.POINTER(_BlockOut)]
         lib.fsr_oracle_block.restype = ctypes.c_int
+        lib.fsr_oracle_block_scaled.argtypes = [ctypes.POINTER(_Params), _DP, _DP, ctypes.POINTER(_BlockOut)]
+        lib.fsr_oracle_block_scaled.restype = ctypes.c_int
+        lib.fsr_oracle_image_reuse.argtypes = [
+            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_long, _DP, _IP, _DP]
+        lib.fsr_oracle_image_reuse.restype = ctypes.c_long
         lib.fsr_oracle_image_blocks.argtypes = [
             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -113,16 +123,22 @@ class OracleLib:
 
     def fsr_block(self, f: np.ndarray, known: np.ndarray, K: int, rho: float = 0.7,
                   gamma: float = 0.5, freq_weight: bool = True,
-                  history: bool = False, conj_pairs: bool = False) -> dict:
+                  history: bool = False, conj_pairs: bool = False, scale=None) -> dict:
         """FSR of one S x S support block (Sec. II).
 
         Returns w, R0, W, seq (u*S+v per iteration, -1 if skipped), p, margin,
         G, g (complex, all pixels), skipped, and with ``history`` the residual
-        spectra R^(nu) for nu = 0..K.
+        spectra R^(nu) for nu = 0..K.  With ``scale`` (S x S, >= 0) the weight
+        of Eq. (5) is scale * w0 and ``known`` is ignored (the pixels with
+        scale 0 are the unknown ones).
         """
         f = np.ascontiguousarray(f, np.float64)
-        known = np.ascontiguousarray(known, np.uint8)
         S = f.shape[0]
+        if scale is not None:
+            scale = np.ascontiguousarray(scale, np.float64)
+            assert scale.shape == (S, S)
+            known = (scale > 0).astype(np.uint8)
+        known = np.ascontiguousarray(known, np.uint8)
         assert f.shape == (S, S) and known.shape == (S, S)
         P = _Params(S, K, rho, gamma, int(bool(freq_weight)), int(bool(conj_pairs)))
         arrs = {n: np.empty((S, S)) for n in ("w", "R0re", "R0im", "Wre", "Wim",
@@ -137,9 +153,12 @@ class OracleLib:
         if history:
             Rhre = np.empty((K + 1, S, S)); Rhim = np.empty((K + 1, S, S))
             o.Rhre, o.Rhim = _dp(Rhre), _dp(Rhim)
-        r = self.lib.fsr_oracle_block(ctypes.byref(P), _dp(f),
-                                     known.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
-                                     ctypes.byref(o))
+        if scale is not None:
+            r = self.lib.fsr_oracle_block_scaled(ctypes.byref(P), _dp(f), _dp(scale), ctypes.byref(o))
+        else:
+            r = self.lib.fsr_oracle_block(ctypes.byref(P), _dp(f),
+                                         known.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                         ctypes.byref(o))
         if r < 0:
             raise ValueError("oracle rejected the block arguments")
         res = dict(
@@ -189,6 +208,36 @@ class OracleLib:
             raise ValueError("oracle rejected the image arguments")
         return dict(target=target, seq=seq[:, :K], margin=margin[:, :K], n_empty=int(r),
                     block_ids=np.arange(n) if ids is None else ids, im_target=im_target)
+
+
+    def fsr_image_reuse(self, img: np.ndarray, mask: np.ndarray, B: int = 4, L: int = 14,
+                        K: int = 100, delta: float = 0.5, rho: float = 0.7, gamma: float = 0.5,
+                        freq_weight: bool = True, nblocks: int = 0) -> dict:
+        """The sequential form that re-uses reconstructed pixels: blocks in
+        raster order, unknown pixels of earlier targets enter later supports
+        with their reconstruction and the weight delta * rho^dist.
+
+        Returns ``out`` (H, W) float64 (the first ``nblocks`` blocks, all when
+        0; NaN on unknown pixels of later blocks), ``seq`` and ``margin``
+        (nblocks, K), ``n_empty``.
+        """
+        img = np.ascontiguousarray(img, np.float32)
+        mask = np.ascontiguousarray(mask, np.uint8)
+        H, Wd = img.shape
+        assert mask.shape == (H, Wd)
+        nall = -(-Wd // B) * -(-H // B)
+        n = nall if nblocks <= 0 else min(int(nblocks), nall)
+        out = np.empty((H, Wd))
+        seq = np.empty((n, max(K, 1)), np.int32)
+        margin = np.empty((n, max(K, 1)))
+        P = _Params(B + 2 * L, K, rho, gamma, int(bool(freq_weight)), 0)
+        r = self.lib.fsr_oracle_image_reuse(
+            img.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+            mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, Wd, Wd, B, L,
+            ctypes.byref(P), float(delta), n, _dp(out), seq.ctypes.data_as(_IP), _dp(margin))
+        if r < 0:
+            raise ValueError("oracle rejected the image arguments")
+        return dict(out=out, seq=seq[:, :K], margin=margin[:, :K], n_empty=int(r))
 
 
 def assemble_image(target: np.ndarray, H: int, Wd: int, B: int) -> np.ndarray:
@@ -249,3 +298,7 @@ def fsr_block(*a, **k):
 
 def fsr_image_blocks(*a, **k):
     return default().fsr_image_blocks(*a, **k)
+
+
+def fsr_image_reuse(*a, **k):
+    return default().fsr_image_reuse(*a, **k)

@@ -433,6 +433,94 @@ def pin_conj_pairs(lib):
     assert np.max(np.abs(res["g"] - f)) <= 1e-10 * 20.0
 
 
+def pin_scaled_weights(lib):
+    """The weight-scaled block routine (re-use form): w = scale * w0 of Eq.
+    (5) with the scale per pixel, R0 = F2{f w} and W = F2{w} against numpy's
+    FFT; scale 1 on the known set is the paper's block routine bit for bit;
+    the energy identity of Eq. (10) holds with the scaled weights."""
+    rng = np.random.default_rng(31)
+    f = rng.uniform(0, 255, (S, S))
+    scale = rng.choice([0.0, 0.25, 0.5, 1.0], (S, S))
+    scale[S // 2, S // 2] = 1.0
+    w0 = lib.spatial_weight(S, 0.7)
+    res = lib.fsr_block(f, None, K=8, scale=scale, history=True)
+    w = scale * w0
+    assert np.allclose(res["w"], w, rtol=0, atol=1e-15)
+    assert np.allclose(res["R0"], np.fft.fft2(f * w), rtol=0, atol=1e-9 * np.abs(np.fft.fft2(f * w)).max())
+    assert np.allclose(res["W"], np.fft.fft2(w), rtol=0, atol=1e-12 * np.abs(np.fft.fft2(w)).max())
+    # the residual is the spectrum of the weighted spatial residual (Eqs. 4, 6)
+    G = _model_history(res, 0.5, 8)
+    for nu in (0, 3, 8):
+        g = np.fft.ifft2(G[nu])
+        ref = np.fft.fft2((f - g) * w)
+        assert np.allclose(res["R_hist"][nu], ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    known = rng.random((S, S)) < 0.5
+    a = lib.fsr_block(f, known, K=10)
+    b = lib.fsr_block(f, None, K=10, scale=known.astype(np.float64))
+    assert np.array_equal(a["seq"], b["seq"]) and np.array_equal(a["g"], b["g"])
+
+
+def _reuse_support(img, mask, out, b, B, L, delta):
+    """Support of block b in the re-use form, built from the definition:
+    known pixels with scale 1, unknown pixels of earlier blocks in raster
+    order with their final reconstruction and scale delta, the rest 0."""
+    H, Wd = img.shape
+    nbx = -(-Wd // B)
+    by, bx = divmod(b, nbx)
+    S_ = B + 2 * L
+    f = np.zeros((S_, S_)); sc = np.zeros((S_, S_))
+    for mm in range(S_):
+        for nn in range(S_):
+            y, x = by * B - L + mm, bx * B - L + nn
+            if not (0 <= y < H and 0 <= x < Wd):
+                continue
+            if mask[y, x]:
+                f[mm, nn], sc[mm, nn] = img[y, x], 1.0
+            elif (y // B) * nbx + (x // B) < b:
+                f[mm, nn], sc[mm, nn] = out[y, x], delta
+    return f, sc, by, bx
+
+
+def pin_reuse_form(lib):
+    """Re-use of reconstructed pixels (the sequential form Sec. II leaves out;
+    reading in fsr_oracle.c): with delta = 0 it is the independent-block
+    oracle bit for bit; with delta > 0 every block equals the block routine
+    run on its support built from the definition (raster order, earlier
+    blocks' reconstructions at weight delta), on a non-square ragged image
+    whose later blocks see earlier reconstructions in their supports."""
+    from oracle import assemble_image  # placement helper only
+    rng = np.random.default_rng(32)
+    H, Wd, B, L, K = 29, 43, 4, 14, 12
+    img = rng.uniform(0, 255, (H, Wd)).astype(np.float32)
+    mask = (rng.random((H, Wd)) < 0.35).astype(np.uint8)
+    ind = assemble_image(lib.fsr_image_blocks(img, mask, B=B, L=L, K=K, threads=1)["target"], H, Wd, B)
+    r0 = lib.fsr_image_reuse(img, mask, B=B, L=L, K=K, delta=0.0)
+    assert np.array_equal(r0["out"], ind)
+    delta = 0.5
+    r = lib.fsr_image_reuse(img, mask, B=B, L=L, K=K, delta=delta)
+    out = r["out"]
+    assert np.all(np.isfinite(out)) and np.array_equal(out[mask == 1], img[mask == 1].astype(np.float64))
+    assert not np.array_equal(out, ind)           # re-used pixels change the result
+    nbx, nby = -(-Wd // B), -(-H // B)
+    for b in range(nbx * nby):
+        f, sc, by, bx = _reuse_support(img, mask, out, b, B, L, delta)
+        res = lib.fsr_block(f, None, K=K, scale=sc)
+        assert np.array_equal(r["seq"][b], res["seq"]), b
+        for a in range(B):
+            for c in range(B):
+                y, x = by * B + a, bx * B + c
+                if y < H and x < Wd and not mask[y, x]:
+                    assert abs(out[y, x] - res["g"][L + a, L + c].real) <= 1e-9 * 255, (b, a, c)
+    # a prefix of the raster order is computed alone, NaN beyond it
+    part = lib.fsr_image_reuse(img, mask, B=B, L=L, K=K, delta=delta, nblocks=nbx * 3 + 2)
+    done = np.zeros((H, Wd), bool)
+    for b in range(nbx * 3 + 2):
+        by, bx = divmod(b, nbx)
+        done[by * B:by * B + B, bx * B:bx * B + B] = True
+    done |= mask == 1
+    assert np.array_equal(part["out"][done], out[done]) and np.all(np.isnan(part["out"][~done]))
+
+
 ALL_PINS = [
     pin_weights_closed_form,
     pin_weight_symmetries,
@@ -451,4 +539,6 @@ ALL_PINS = [
     pin_block_ignores_unknown_values,
     pin_small_supports,
     pin_conj_pairs,
+    pin_scaled_weights,
+    pin_reuse_form,
 ]

@@ -43,14 +43,23 @@ MUTANTS = {
     "inverse_sign": ("double c = Tre[t], d = -Tim[t];", "double c = Tre[t], d = Tim[t];"),
     "inverse_scale": ("if (o->gre) o->gre[m * S + n] = sr / (double)SS;",
                       "if (o->gre) o->gre[m * S + n] = sr;"),
-    "unknown_read": ("x[i] = known[i] ? f[i] * w[i] : 0.0;", "x[i] = f[i] * w[i];"),
-    "weight_everywhere": ("w[i] = known[i] ? w0[i] : 0.0;", "w[i] = w0[i];"),
+    "unknown_read": ("x[i] = scale[i] > 0.0 ? f[i] * w[i] : 0.0;", "x[i] = f[i] * w[i];"),
+    "weight_everywhere": ("w[i] = scale[i] > 0.0 ? scale[i] * w0[i] : 0.0;", "w[i] = w0[i];"),
+    "scale_ignored": ("w[i] = scale[i] > 0.0 ? scale[i] * w0[i] : 0.0;", "w[i] = scale[i] > 0.0 ? w0[i] : 0.0;"),
     # the conjugate-pair ablation
     "pair_model_not_conjugate": ("Gim[sel_conj] -= cim * (double)SS;", "Gim[sel_conj] += cim * (double)SS;"),
     "pair_second_shift_sign": ("const int d2 = ((k + su) % S) * S + (l + sv) % S;",
                                "const int d2 = ((k + S - su) % S) * S + (l + sv) % S;"),
     "pair_update_diff_sign": ("ur = cre * sr - cim * di;", "ur = cre * sr + cim * di;"),
     "pair_selfconj_doubled": ("if (sel_conj == sel) {", "if (0) {"),
+    # the re-use form (reconstructed pixels of earlier blocks)
+    "reuse_no_delta": ("                        sc = delta;", "                        sc = 1.0;"),
+    "reuse_own_block": ("} else if ((y / B) * nbx + (x / B) < b) {", "} else if ((y / B) * nbx + (x / B) <= b) {"),
+    "reuse_column_order": ("} else if ((y / B) * nbx + (x / B) < b) {",
+                           "} else if ((x / B) * nby + (y / B) < bx * nby + by) {"),
+    "reuse_origin": ("        const long x0 = bx * B - L;", "        const long x0 = bx * B - L + 1;"),
+    "reuse_value_from_input": ("                        v = out[y * Wd + x];",
+                               "                        v = (double)img[y * pitch + x];"),
 }
 
 
