@@ -431,11 +431,18 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
  * out: H x Wd (row pitch Wd) reconstruction of blocks 0 .. nblocks-1 (known
  * pixels copied, NaN on pixels of later blocks); nblocks <= 0: all blocks.
  * seq, margin: optional nblocks*K.  Single-threaded (each block depends on
- * the ones before it).  Returns the number of blocks without any known or
- * re-used pixel, or -1 on error. */
+ * the ones before it).
+ * given: optional H x Wd reconstruction (row pitch Wd) to take the re-used
+ * values from instead of the routine's own earlier results; each block then
+ * depends on `given` only and the blocks run in parallel (nthreads).  With
+ * given = the routine's own result every block sees the same support as in
+ * the sequential run.
+ * Returns the number of blocks without any known or re-used pixel, or -1 on
+ * error. */
 long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
                             int H, int Wd, int pitch, int B, int L,
                             const fsr_oracle_params *P, double delta, long nblocks,
+                            const double *given, int nthreads,
                             double *out, int *seq, double *margin)
 {
     if (!img || !mask || !P || !out || H <= 0 || Wd <= 0 || pitch < Wd ||
@@ -447,14 +454,21 @@ long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
     for (long y = 0; y < H; ++y)
         for (long x = 0; x < Wd; ++x)
             out[y * Wd + x] = mask[y * pitch + x] ? (double)img[y * pitch + x] : NAN;
-    double *f = malloc(sizeof(double) * S * S), *scale = malloc(sizeof(double) * S * S);
-    double *gre = malloc(sizeof(double) * S * S);
-    unsigned char *need = calloc((size_t)S * S, 1);
-    for (int a = 0; a < B; ++a)
-        for (int c = 0; c < B; ++c) need[(L + a) * S + (L + c)] = 1;
+    const double *src = given ? given : out;   /* where re-used values come from */
     long n_empty = 0;
     int bad = 0;
-    for (long b = 0; b < nblocks && !bad; ++b) {
+    if (nthreads <= 0) nthreads = fsr_oracle_max_threads();
+    if (!given) nthreads = 1;                    /* the sequential form */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads) reduction(+ : n_empty) reduction(| : bad)
+#endif
+    for (long b = 0; b < nblocks; ++b) {
+        if (bad) continue;
+        double *f = malloc(sizeof(double) * S * S), *scale = malloc(sizeof(double) * S * S);
+        double *gre = malloc(sizeof(double) * S * S);
+        unsigned char *need = calloc((size_t)S * S, 1);
+        for (int a = 0; a < B; ++a)
+            for (int c = 0; c < B; ++c) need[(L + a) * S + (L + c)] = 1;
         const long by = b / nbx;          /* raster order: block row, then column */
         const long bx = b - by * nbx;
         const long y0 = by * B - L;       /* support origin (Sec. III-A) */
@@ -468,7 +482,7 @@ long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
                         v = (double)img[y * pitch + x];
                         sc = 1.0;
                     } else if ((y / B) * nbx + (x / B) < b) {    /* reconstructed by an earlier block */
-                        v = out[y * Wd + x];
+                        v = src[y * Wd + x];
                         sc = delta;
                     }
                 }
@@ -490,7 +504,7 @@ long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
                 const long y = y0 + L + a, x = x0 + L + c;
                 if (y < H && x < Wd && !mask[y * pitch + x]) out[y * Wd + x] = gre[(L + a) * S + (L + c)];
             }
+        free(f); free(scale); free(gre); free(need);
     }
-    free(f); free(scale); free(gre); free(need);
     return bad ? -1 : n_empty;
 }

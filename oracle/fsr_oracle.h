@@ -97,11 +97,14 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
  * enter later supports with their reconstruction and the weight
  * delta * rho^dist.  out: H x Wd reconstruction of the first nblocks blocks
  * (<= 0: all; NaN on unknown pixels of later blocks); seq, margin optional
- * (nblocks*K).  Returns the number of blocks without any known or re-used
- * pixel, or -1 on error. */
+ * (nblocks*K).  given: optional H x Wd reconstruction the re-used values are
+ * taken from instead (each block then depends on it alone; nthreads OpenMP
+ * threads, <= 0: default).  Returns the number of blocks without any known
+ * or re-used pixel, or -1 on error. */
 long fsr_oracle_image_reuse(const float *img, const unsigned char *mask,
                             int H, int Wd, int pitch, int B, int L,
                             const fsr_oracle_params *P, double delta, long nblocks,
+                            const double *given, int nthreads,
                             double *out, int *seq, double *margin);
 
 /* Number of OpenMP threads the image routine would use by default. */

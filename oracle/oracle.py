@@ -86,7 +86,7 @@ class OracleLib:
         lib.fsr_oracle_image_reuse.argtypes = [
             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-            ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_long, _DP, _IP, _DP]
+            ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_long, _DP, ctypes.c_int, _DP, _IP, _DP]
         lib.fsr_oracle_image_reuse.restype = ctypes.c_long
         lib.fsr_oracle_image_blocks.argtypes = [
             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
@@ -212,14 +212,16 @@ class OracleLib:
 
     def fsr_image_reuse(self, img: np.ndarray, mask: np.ndarray, B: int = 4, L: int = 14,
                         K: int = 100, delta: float = 0.5, rho: float = 0.7, gamma: float = 0.5,
-                        freq_weight: bool = True, nblocks: int = 0) -> dict:
+                        freq_weight: bool = True, nblocks: int = 0, given=None, threads: int = 0) -> dict:
         """The sequential form that re-uses reconstructed pixels: blocks in
         raster order, unknown pixels of earlier targets enter later supports
         with their reconstruction and the weight delta * rho^dist.
 
         Returns ``out`` (H, W) float64 (the first ``nblocks`` blocks, all when
         0; NaN on unknown pixels of later blocks), ``seq`` and ``margin``
-        (nblocks, K), ``n_empty``.
+        (nblocks, K), ``n_empty``.  With ``given`` (H, W) the re-used values
+        come from that reconstruction instead of the routine's own earlier
+        results (every block on its own, ``threads`` OpenMP threads).
         """
         img = np.ascontiguousarray(img, np.float32)
         mask = np.ascontiguousarray(mask, np.uint8)
@@ -234,7 +236,9 @@ class OracleLib:
         r = self.lib.fsr_oracle_image_reuse(
             img.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, Wd, Wd, B, L,
-            ctypes.byref(P), float(delta), n, _dp(out), seq.ctypes.data_as(_IP), _dp(margin))
+            ctypes.byref(P), float(delta), n,
+            _dp(np.ascontiguousarray(given, np.float64)) if given is not None else None, int(threads),
+            _dp(out), seq.ctypes.data_as(_IP), _dp(margin))
         if r < 0:
             raise ValueError("oracle rejected the image arguments")
         return dict(out=out, seq=seq[:, :K], margin=margin[:, :K], n_empty=int(r))

@@ -511,6 +511,10 @@ def pin_reuse_form(lib):
                 y, x = by * B + a, bx * B + c
                 if y < H and x < Wd and not mask[y, x]:
                     assert abs(out[y, x] - res["g"][L + a, L + c].real) <= 1e-9 * 255, (b, a, c)
+    # with the sequential result given as the source of re-used values, every
+    # block sees the same support: the parallel evaluation is bit-identical
+    par = lib.fsr_image_reuse(img, mask, B=B, L=L, K=K, delta=delta, given=out, threads=3)
+    assert np.array_equal(par["out"], out) and np.array_equal(par["seq"], r["seq"])
     # a prefix of the raster order is computed alone, NaN beyond it
     part = lib.fsr_image_reuse(img, mask, B=B, L=L, K=K, delta=delta, nblocks=nbx * 3 + 2)
     done = np.zeros((H, Wd), bool)

@@ -58,7 +58,7 @@ MUTANTS = {
     "reuse_column_order": ("} else if ((y / B) * nbx + (x / B) < b) {",
                            "} else if ((x / B) * nby + (y / B) < bx * nby + by) {"),
     "reuse_origin": ("        const long x0 = bx * B - L;", "        const long x0 = bx * B - L + 1;"),
-    "reuse_value_from_input": ("                        v = out[y * Wd + x];",
+    "reuse_value_from_input": ("                        v = src[y * Wd + x];",
                                "                        v = (double)img[y * pitch + x];"),
 }
 
