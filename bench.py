@@ -314,6 +314,52 @@ def _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch):
     return rows
 
 
+def _measure_reuse(fsr, handle, img, mask, d_img, d_mask, d_out, stream, flush, torch, check_rows=8):
+    """Re-use of reconstructed pixels (the original FSR's sequential form,
+    which the paper leaves out) on the 1080p frame, K = 100, delta = 0.5:
+    one launch per wavefront of the raster order.  Time per frame and PSNR
+    beside the paper's independent blocks, and every block of the first
+    check_rows block rows against the oracle on the same supports (the
+    re-used values taken from this reconstruction)."""
+    truth = d_img.double()
+    rows = {}
+    nbx, nby = -(-W // B), -(-H // B)
+    slope = -(-L // B) + 1
+    for delta in (0.0, 0.5):
+        pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, reuse=delta)
+        fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        ts = []
+        for i in range(3):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        mse = float(torch.mean((d_out.double() - truth) ** 2))
+        ms = float(np.median(ts))
+        row = {"ms_per_frame": ms, "mp_per_s": H * W / 1e6 / (ms / 1e3), "psnr_db": 10 * np.log10(255.0 ** 2 / mse)}
+        if delta > 0:
+            row["launches"] = slope * (nby - 1) + nbx
+            import oracle
+            oracle.build()
+            got = d_out.cpu().numpy().astype(np.float64)
+            nb = check_rows * nbx
+            ref = oracle.fsr_image_reuse(img, mask, B=B, L=L, K=K_ITERS, delta=delta, rho=RHO, gamma=GAMMA,
+                                         nblocks=nb, given=got)["out"]
+            part = slice(0, check_rows * B)
+            unk = mask[part] == 0
+            d = np.abs(got[part] - ref[part])[unk]
+            row["parity_first_rows"] = {"block_rows": check_rows, "blocks": nb,
+                                        "frac_unknown_within_0.5": float(np.mean(d <= 0.5)),
+                                        "max_abs": float(d.max()),
+                                        "note": "each block against the oracle on the same supports"}
+        rows["independent" if delta == 0 else f"reuse_delta_{delta}"] = row
+    return rows
+
+
 def _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch):
     """Reconstruction quality (PSNR against the ground truth, K = 100) of the
     1080p frame over the spatial weight decay rho and the damping gamma."""
@@ -631,6 +677,8 @@ def main():
         line["param_sweep"] = _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch)
         line["s_sweep"] = _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
         line["ablation_update"] = _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
+        line["reuse_reconstructed"] = _measure_reuse(fsr, handle, img, mask, d_img, d_mask, d_out, stream, flush,
+                                                     torch)
     if world == 1 and not args.no_batch:
         line["batch"] = _measure_batch(fsr, handle, dev, torch)
     if world == 1 and args.serve_seconds > 0:

@@ -93,6 +93,15 @@ typedef struct fsr_params {
                          block b = by*ceil(width/B) + bx): the selected u*S+v of each
                          iteration, -1 for a block without known pixels; NULL = off */
     int update;       /* FSR_UPDATE_SINGLE (0, zero-initialised default) or FSR_UPDATE_CONJ_PAIR */
+    float reuse;      /* re-use weight delta in [0, 1].  0 (zero-initialised default): the
+                         paper's independent blocks (Sec. II refrains from re-using
+                         reconstructed pixels).  > 0: the sequential form of the original
+                         FSR: blocks in raster order, and an unknown pixel of an earlier
+                         block's target takes part in later supports with its
+                         reconstruction and the weight delta * rho^dist of Eq. (5).
+                         Runs as one launch per wavefront of blocks (t = a*by + bx,
+                         a = ceil(L/B) + 1); single-image entry points, S = 32,
+                         FSR_UPDATE_SINGLE, FSR_FP32 / FSR_FP64_DEBUG only. */
 } fsr_params;
 
 typedef struct fsr_handle fsr_handle;
@@ -124,7 +133,8 @@ const char *fsr_last_error(const fsr_handle *h);
  * Errors: INVALID_ARG (NULL pointers, sizes <= 0, pitch < width, overlap,
  * parameters out of range), UNSUPPORTED (a support or block size not listed at
  * fsr_params.border, a tensor-core mode with S < 32, FSR_UPDATE_CONJ_PAIR
- * outside S = 32, B = 4, FSR_FP32 / FSR_FP64_DEBUG),
+ * outside S = 32, B = 4, FSR_FP32 / FSR_FP64_DEBUG, reuse > 0 outside S = 32,
+ * FSR_UPDATE_SINGLE, FSR_FP32 / FSR_FP64_DEBUG),
  * CUDA (launch failure). */
 int fsr_reconstruct(fsr_handle *h, const float *img, const uint8_t *mask,
                     int height, int width, int pitch, const fsr_params *p,
@@ -195,7 +205,7 @@ typedef struct fsr_image_desc {
 
 /* Schedule of the persistent batch launch. */
 typedef struct fsr_schedule {
-    int warps;   /* warps per CTA = support blocks in flight per CTA (FP32: 16, or 8/12 for B = 4; FP64: 4) */
+    int warps;   /* warps per CTA = support blocks in flight per CTA (FP32: 8, or 12/16 for B = 4; FP64: 4) */
     int chunk;   /* blocks a warp takes per counter increment, 1..64 */
 } fsr_schedule;
 

@@ -565,30 +565,85 @@ __device__ __forceinline__ unsigned load_support(const ImageArgs& a, int y0, int
     return known;
 }
 
+// Re-use of reconstructed pixels (the sequential form of the original FSR,
+// which Sec. II leaves out): blocks run in raster order, and an unknown pixel
+// of an earlier block's target takes part in later supports with its
+// reconstruction and the weight delta rho^dist.  prev: the output image
+// (same pitch), whose earlier targets are complete when the block runs.
+struct ReuseCtx {
+    const float* prev;
+    float delta;
+    int by, bx, B;
+};
+
+// a1 for the re-use form (plain loads): raw values of column `lane` of the
+// support, 0 where neither known nor re-used; known bits in the return
+// value, re-used bits (unknown pixels of blocks before (by, bx) in raster
+// order) in `reused`.
+template <typename T>
+__device__ __forceinline__ unsigned load_support_reuse(const ImageArgs& a, const ReuseCtx& ru, int y0, int x0,
+                                                       int lane, T (&zr)[S], unsigned& reused) {
+    unsigned known = 0, reu = 0;
+    const int xc = x0 + lane;
+    const bool xin = (unsigned)xc < (unsigned)a.W;
+    const int pbx = xin ? xc / ru.B : 0;
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        const int y = y0 + m;
+        bool kn = false, re = false;
+        float fv = 0.f;
+        if (xin && (unsigned)y < (unsigned)a.H) {
+            const size_t off = (size_t)y * a.pitch + xc;
+            kn = __ldg(a.mask + off) != 0;
+            const int pby = y / ru.B;
+            re = !kn && (pby < ru.by || (pby == ru.by && pbx < ru.bx));
+            // earlier targets were written by earlier launches: read through L2
+            fv = kn ? __ldg(a.img + off) : (re ? __ldcg(ru.prev + off) : 0.f);
+        }
+        zr[m] = (kn || re) ? T(fv) : T(0);
+        known |= kn ? (1u << m) : 0u;
+        reu |= re ? (1u << m) : 0u;
+    }
+    reused = reu;
+    return known;
+}
+
 // a1-a3 up to the packed spectrum: load the support (lane n = column n),
 // weight it and transform z = x + j alpha w.  On return (when some pixel is
 // known) lane k holds Z[k][0..31] = F2{z} row k in zr/zi; inv2alpha =
 // 1 / (2 alpha); swd: sum of w in FP64 (precision study only).  Wd: this
 // warp's scratch (the support tile and the transpose pass through it).
-template <typename T, Dft DFT>
+template <typename T, Dft DFT, bool REUSE = false>
 __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int x0, int lane,
                                                 const T* __restrict__ sw0,
                                                 typename Vec2<T>::type* Wd, const unsigned char* tctab,
                                                 const unsigned char* tile,
                                                 T (&zr)[S], T (&zi)[S], BlockState<T>& st, T& inv2alpha_out,
-                                                double& swd_out) {
+                                                double& swd_out, const ReuseCtx* ru = nullptr) {
     using T2 = typename Vec2<T>::type;
-    const unsigned known = load_support<T>(a, y0, x0, lane, tile, zr);
+    unsigned reused = 0;
+    unsigned known;
+    if constexpr (REUSE) known = load_support_reuse<T>(a, *ru, y0, x0, lane, zr, reused);
+    else known = load_support<T>(a, y0, x0, lane, tile, zr);
+    // Eq. (5): w0 on known pixels, delta w0 on re-used ones, 0 elsewhere
+    auto weight = [&](int m) -> T {
+        if constexpr (REUSE)
+            return ((known >> m) & 1u) ? sw0[m * S + lane]
+                                       : (((reused >> m) & 1u) ? T(ru->delta) * sw0[m * S + lane] : T(0));
+        else
+            return ((known >> m) & 1u) ? sw0[m * S + lane] : T(0);
+    };
+    const unsigned avail = known | reused;
     T sw = T(0), sfw = T(0);
     double swd = 0.0;   // precision study: W[0][0] = sum of w in FP64
 #pragma unroll
     for (int m = 0; m < S; ++m) {
-        const T w = ((known >> m) & 1u) ? sw0[m * S + lane] : T(0);
+        const T w = weight(m);
         sw += w;
         sfw += w * zr[m];
         if constexpr (DFT != Dft::SIMT) swd += double(w);
     }
-    if (__ballot_sync(FULL, known != 0) == 0) return false;
+    if (__ballot_sync(FULL, avail != 0) == 0) return false;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sw += __shfl_xor_sync(FULL, sw, o);
@@ -604,8 +659,8 @@ __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int 
     unsigned dmax = 0;
 #pragma unroll
     for (int m = 0; m < S; ++m) {
-        const bool kn = (known >> m) & 1u;
-        const T w = kn ? sw0[m * S + lane] : T(0);
+        const bool kn = (avail >> m) & 1u;
+        const T w = weight(m);
         const T d = zr[m] - mu;
         zr[m] = kn ? d * w : T(0);
         zi[m] = w;
@@ -652,16 +707,18 @@ __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int 
 // a1-a3: load the support (lane n = column n), weight it, transform it.
 // On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
 // row k in zr/zi and the W rows are in Wd (layout of WRow<T>).
-template <typename T, int WS, Dft DFT>
+template <typename T, int WS, Dft DFT, bool REUSE = false>
 __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
                                               const T* __restrict__ sw0,
                                               typename Vec2<T>::type* Wd, const unsigned char* tctab,
                                               const unsigned char* tile,
-                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st) {
+                                              T (&zr)[S], T (&zi)[S], BlockState<T>& st,
+                                              const ReuseCtx* ru = nullptr) {
     using T2 = typename Vec2<T>::type;
     T inv2alpha;
     double swd;
-    if (!transform_block<T, DFT>(a, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st, inv2alpha, swd)) return false;
+    if (!transform_block<T, DFT, REUSE>(a, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st, inv2alpha, swd, ru))
+        return false;
 
     // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,  W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha)
     const int src = (S - lane) & (S - 1);
@@ -1209,12 +1266,12 @@ __device__ __forceinline__ void empty_block(int16_t* seq, int K, unsigned long l
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
 // With a tile context the support comes in by TMA; returns false when the
 // bounded wait for it gave up (the warp then stops taking blocks).
-template <typename T, int B, Dft DFT = Dft::SIMT, bool CONJ = false>
+template <typename T, int B, Dft DFT = Dft::SIMT, bool CONJ = false, bool REUSE = false>
 __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
                                               const unsigned char* tctab, const TileReq& tr,
-                                              unsigned long long* empty, int lane) {
+                                              unsigned long long* empty, int lane, float delta = 0.f) {
     constexpr int P = TargetPix<B>::P;
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -1257,7 +1314,16 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
             empty_block(seq, im.K, empty);
         }
     } else {
-        if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
+        ReuseCtx ru;
+        if constexpr (REUSE) {
+            ru.prev = im.out;
+            ru.delta = delta;
+            ru.by = by;
+            ru.bx = bx;
+            ru.B = B;
+        }
+        if (prepare_block<T, SmemLayout<T>::WS, DFT, REUSE>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st,
+                                                             REUSE ? &ru : nullptr)) {
             iterate<B, false, CONJ>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
             __syncwarp();   // W area free for the next block
         } else if (lane == 0) {
@@ -1403,6 +1469,46 @@ fsr_batch_kernel(const BatchArgs a) {
         if (!ok) break;   // a tile wait gave up: this warp takes no more blocks
         if constexpr (ONE_ROUND) break;
     }
+}
+
+// Re-use form: one launch per wavefront t of the raster order.  Block
+// (by, bx) runs in wavefront t = a by + bx with a = ceil(L / B) + 1, so every
+// block of the raster order before it whose target meets its support (rows
+// by - ceil(L/B) .. by, columns up to bx + ceil(L/B)) ran in an earlier
+// launch, and no two blocks of one launch touch each other's supports.
+struct ReuseLaunch {
+    ImageArgs im;
+    MethodArgs mth;
+    float delta;            // re-use weight (0 < delta <= 1)
+    int t;                  // wavefront
+    int slope;              // a = ceil(L / B) + 1
+    int by_lo, count;       // blocks by_lo .. by_lo + count - 1 (by), bx = t - a by
+    unsigned long long* empty;
+};
+
+template <typename T, int B, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
+fsr_reuse_kernel(const __grid_constant__ ReuseLaunch a) {
+    using T2 = typename Vec2<T>::type;
+    using Lay = SmemLayout<T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* sw0 = reinterpret_cast<T*>(smem + Lay::w0_off);
+    T* swf = reinterpret_cast<T*>(smem + Lay::wf_off);
+    T2* scs = reinterpret_cast<T2*>(smem + Lay::cs_off);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
+    T2* rowbuf = Wd + Lay::w_elems;
+    cta_tables<T>(a.mth, sw0, swf, scs);
+    __syncthreads();
+    const int j = blockIdx.x * WARPS + warp;
+    if (j >= a.count) return;
+    const int by = a.by_lo + j;
+    const int bx = a.t - a.slope * by;
+    TileReq tr;
+    tr.maps = nullptr;
+    process_block<T, B, Dft::SIMT, false, true>(a.im, (long long)by * a.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0,
+                                                swf, scs, Wd, rowbuf, nullptr, tr, a.empty, lane, a.delta);
 }
 
 }  // namespace fsrk

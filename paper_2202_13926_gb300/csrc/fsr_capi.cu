@@ -96,6 +96,11 @@ int check_method(fsr_handle* h, const fsr_params* p) {
     if (p->update == FSR_UPDATE_CONJ_PAIR &&
         (S != fsrk::S || p->block != 4 || (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)))
         return fail(h, FSR_ERR_UNSUPPORTED, "the conjugate-pair update is built for S = 32, B = 4, FP32 and FP64");
+    if (!(p->reuse >= 0.f && p->reuse <= 1.f)) return fail(h, FSR_ERR_INVALID_ARG, "reuse must be in [0, 1]");
+    if (p->reuse > 0.f && (S != fsrk::S || p->update != FSR_UPDATE_SINGLE ||
+                           (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)))
+        return fail(h, FSR_ERR_UNSUPPORTED,
+                    "re-use of reconstructed pixels is built for S = 32, FSR_UPDATE_SINGLE, FP32 and FP64");
     return FSR_OK;
 }
 
@@ -250,8 +255,38 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
     return ok(h);
 }
 
+// Re-use form: one launch per wavefront t = a*by + bx (a = ceil(L/B) + 1) of
+// the raster order; block (by, bx) of launch t reads the targets of the
+// launches before it.
+int enqueue_reuse(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                  const fsr_params* p, float* out, cudaStream_t stream) {
+    fsrk::ReuseLaunch a;
+    std::memset(&a, 0, sizeof a);
+    a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
+    a.mth = method_args(p);
+    a.delta = p->reuse;
+    a.slope = (p->border + p->block - 1) / p->block + 1;
+    a.empty = h->d_empty;
+    const int nbx = a.im.nbx, nby = (height + p->block - 1) / p->block;
+    const long long waves = (long long)a.slope * (nby - 1) + nbx;
+    for (long long t = 0; t < waves; ++t) {
+        // blocks with a*by + bx = t, 0 <= bx < nbx, 0 <= by < nby
+        const long long lo_num = t - (nbx - 1);
+        const long long by_lo = lo_num <= 0 ? 0 : (lo_num + a.slope - 1) / a.slope;
+        const long long by_hi = std::min<long long>(nby - 1, t / a.slope);
+        if (by_hi < by_lo) continue;
+        a.t = (int)t;
+        a.by_lo = (int)by_lo;
+        a.count = (int)(by_hi - by_lo + 1);
+        const cudaError_t e = fsrk::launch_reuse(a, p->block, p->precision == FSR_FP64_DEBUG, stream);
+        if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "re-use launch %lld failed: %s", t, cudaGetErrorString(e));
+    }
+    return ok(h);
+}
+
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
                    const fsr_params* p, float* out, cudaStream_t stream) {
+    if (p->reuse > 0.f) return enqueue_reuse(h, img, mask, height, width, pitch, p, out, stream);
     if (p->precision == FSR_FP32 || p->block + 2 * p->border != fsrk::S || p->update == FSR_UPDATE_CONJ_PAIR)
         return enqueue_single_fp32(h, img, mask, height, width, pitch, p, out, stream);
     fsrk::KernelArgs a;
@@ -295,6 +330,8 @@ int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params*
     if (r != FSR_OK) return r;
     if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
         return fail(h, FSR_ERR_UNSUPPORTED, "the batch form runs FSR_FP32 or FSR_FP64_DEBUG");
+    if (p->reuse > 0.f)
+        return fail(h, FSR_ERR_UNSUPPORTED, "re-use of reconstructed pixels runs in the single-image entry points");
     for (int i = 0; i < n; ++i) {
         r = check_image(h, d[i].img, d[i].mask, d[i].out, d[i].height, d[i].width, d[i].pitch, d[i].iters, true, i);
         if (r != FSR_OK) return r;
@@ -474,6 +511,7 @@ int fsr_create(const fsr_config* cfg, fsr_handle** out) {
         return fail(nullptr, FSR_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only",
                     cfg->device, prop.major, prop.minor);
     if ((e = fsrk::configure_fp32_batch()) != cudaSuccess || (e = fsrk::configure_small()) != cudaSuccess ||
+        (e = fsrk::configure_reuse()) != cudaSuccess ||
         (e = fsrk::configure_fp32_sched()) != cudaSuccess || (e = fsrk::configure_fp64()) != cudaSuccess ||
         (e = fsrk::configure_fp64_batch()) != cudaSuccess || (e = fsrk::configure_fp32_tc()) != cudaSuccess ||
         (e = fsrk::configure_conj()) != cudaSuccess || (e = fsrk::configure_fp32_short()) != cudaSuccess)

@@ -89,6 +89,8 @@ extern "C" int fsr_reconstruct_batch_static(int n, const fsr_image_desc* d, cons
         return report(err, err_len, FSR_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
     if (p->update != FSR_UPDATE_SINGLE)
         return report(err, err_len, FSR_ERR_UNSUPPORTED, "the allocation-free entry point runs FSR_UPDATE_SINGLE only");
+    if (p->reuse != 0.f)
+        return report(err, err_len, FSR_ERR_UNSUPPORTED, "the allocation-free entry point runs independent blocks (reuse = 0)");
     for (int i = 0; i < n; ++i) {
         const fsr_image_desc& x = d[i];
         if (!x.img || !x.mask || !x.out || x.height <= 0 || x.width <= 0 || x.pitch < x.width || x.iters < 0 ||

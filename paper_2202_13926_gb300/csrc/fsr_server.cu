@@ -347,6 +347,8 @@ int fsr_server_create(fsr_handle* h, const fsr_server_config* cfg, const fsr_par
     if (r != FSR_OK) return r;
     if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
         return fsri::fail(h, FSR_ERR_UNSUPPORTED, "the server runs FSR_FP32 or FSR_FP64_DEBUG");
+    if (p->reuse > 0.f)
+        return fsri::fail(h, FSR_ERR_UNSUPPORTED, "re-use of reconstructed pixels runs in the single-image entry points");
     if (cfg->pool_bytes < (1u << 20) || cfg->max_inflight < 1 || cfg->streams < 1 || cfg->streams > 8)
         return fsri::fail(h, FSR_ERR_INVALID_ARG, "pool_bytes >= 1 MiB, max_inflight >= 1 and 1 <= streams <= 8");
     int prev = 0;

@@ -72,7 +72,7 @@ class fsr_params(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("iters", ctypes.c_int),
                 ("rho", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("freq_weight", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seq_out", ctypes.c_void_p), ("update", ctypes.c_int)]
+                ("seq_out", ctypes.c_void_p), ("update", ctypes.c_int), ("reuse", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -150,12 +150,14 @@ def _check(code: int, handle) -> None:
 
 
 def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=True,
-                precision="fp32", seq_out=None, update="single") -> fsr_params:
+                precision="fp32", seq_out=None, update="single", reuse=0.0) -> fsr_params:
     """fsr_params of include/fsr.h: B = block, L = border (support S = B + 2L:
     32, 24, 16, 8 or 4), K = iters, rho-hat, gamma, w_f switch, precision
     ("fp32", "fp64", "tc_bf16x3", "tc_tf32"), optional int16 CUDA tensor for
     the selected indices, update ("single": the paper's; "conj_pair": the
-    ablation of the original FSR's real model)."""
+    ablation of the original FSR's real model), reuse (delta: 0 = the paper's
+    independent blocks; > 0 re-uses reconstructed pixels of earlier blocks
+    with that weight, the original FSR's sequential form)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     upd = UPDATES[update] if isinstance(update, str) else int(update)
     seq_ptr = None
@@ -166,7 +168,7 @@ def make_params(block=4, border=14, iters=100, rho=0.7, gamma=0.5, freq_weight=T
             raise ValueError("seq_out must be a contiguous int16 CUDA tensor")
         seq_ptr = seq_out.data_ptr()
     return fsr_params(int(block), int(border), int(iters), float(rho), float(gamma),
-                      int(bool(freq_weight)), prec, seq_ptr, upd)
+                      int(bool(freq_weight)), prec, seq_ptr, upd, float(reuse))
 
 
 def fsr_num_blocks(height: int, width: int, block: int) -> int:
