@@ -88,7 +88,8 @@ typedef struct fsr_params {
     float rho;        /* rho-hat of Eq. (5), in (0, 1] */
     float gamma;      /* gamma of Eqs. (11)-(12), in (0, 1] */
     int freq_weight;  /* 1: objective w_f |R_w|^2 (Eq. 8, paper default); 0: |R_w|^2 */
-    int precision;    /* FSR_FP32, FSR_FP64_DEBUG, or (single image, B = 4) FSR_TC_BF16X3 / FSR_TC_TF32 */
+    int precision;    /* FSR_FP32, FSR_FP64_DEBUG, or (single image, B = 4, K <= 256) FSR_TC_BF16X3 /
+                         FSR_TC_TF32: both 2-D DFTs as tcgen05 tensor-core GEMMs */
     int16_t *seq_out; /* optional DEVICE buffer of N*K entries (N = number of blocks,
                          block b = by*ceil(width/B) + bx): the selected u*S+v of each
                          iteration, -1 for a block without known pixels; NULL = off */

@@ -212,212 +212,15 @@ __device__ __forceinline__ double warp_max(double x) {
     return x;
 }
 
-// ---------------------------------------------------------------- forward
-// transform on tensor cores (precision study).  Both passes of the 2-D DFT
-// are one real GEMM  D (32 x 64) = A (32 x 64) . M (64 x 64)  with
-//   A = [Re | Im] of the 32 x 32 complex input (rows m, columns n),
-//   M = [[Fr, Fi], [-Fi, Fr]],  F[n][l] = e^{-j 2 pi n l / 32} (symmetric),
-// so D = [Re | Im] of (input . F).  Pass 1 gives Y = z F (DFT over n); pass
-// 2 takes A = Y^T and gives Z^T = Y^T F, i.e. Z = F Y F (DFT over both axes).
-// Operands are rounded to TF32, or split into BF16 hi + lo with the three
-// products hi.hi + hi.lo + lo.hi; accumulation is FP32.
+// Arithmetic of the 2-D DFTs: SIMT FFTs, or (precision study) GEMMs on the
+// tensor cores with TF32 operands or BF16 hi/lo split products (the
+// tcgen05 transform of fsr_tc5.cuh).
 enum class Dft { SIMT = 0, TF32 = 1, BF16X3 = 2 };
 
-constexpr int TC_AS = 68;   // row stride (floats) of A and of M^T in TF32 form
-constexpr int TC_HS = 72;   // row stride (bf16 elements) of the BF16 hi/lo arrays
-
-template <Dft D> struct TcTable;
-template <> struct TcTable<Dft::SIMT> { static constexpr size_t bytes = 0; };
-template <> struct TcTable<Dft::TF32> { static constexpr size_t bytes = sizeof(float) * 64 * TC_AS; };
-template <> struct TcTable<Dft::BF16X3> { static constexpr size_t bytes = 2 * sizeof(uint16_t) * 64 * TC_HS; };
-
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-    uint16_t r;
-    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float bf16_value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// M^T (n-major: row = output column nn, column = inner index kk) of the
-// real-expanded DFT matrix, per CTA.
-template <Dft D>
-__device__ __forceinline__ void tc_table(unsigned char* tab) {
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-        const int nn = i / 64, kk = i % 64;
-        const int n = kk & 31, l = nn & 31, t = (n * l) & 31;
-        const float c = (float)cos_2pi32(t), sn = (float)sin_2pi32(t);
-        // M[kk][nn]: [[cos, -sin], [sin, cos]]
-        const float v = (kk < 32) ? ((nn < 32) ? c : -sn) : ((nn < 32) ? sn : c);
-        if (D == Dft::TF32) {
-            reinterpret_cast<uint32_t*>(tab)[nn * TC_AS + kk] = tf32_bits(v);
-        } else if (D == Dft::BF16X3) {
-            uint16_t* hi = reinterpret_cast<uint16_t*>(tab);
-            uint16_t* lo = hi + 64 * TC_HS;
-            const uint16_t h = bf16_bits(v);
-            hi[nn * TC_HS + kk] = h;
-            lo[nn * TC_HS + kk] = bf16_bits(v - bf16_value(h));
-        }
-    }
-}
-
-// Stage the 32 x 64 operand A = [re | im] of this warp's block in shared
-// memory (rows r, re at column c, im at column 32 + c), in the GEMM's format.
-template <Dft D>
-__device__ __forceinline__ void tc_put(unsigned char* buf, int r, int c, float re, float im) {
-    if (D == Dft::TF32) {
-        uint32_t* a = reinterpret_cast<uint32_t*>(buf);
-        a[r * TC_AS + c] = tf32_bits(re);
-        a[r * TC_AS + 32 + c] = tf32_bits(im);
-    } else {
-        uint16_t* hi = reinterpret_cast<uint16_t*>(buf);
-        uint16_t* lo = hi + 32 * TC_HS;
-        const uint16_t hr = bf16_bits(re), hm = bf16_bits(im);
-        hi[r * TC_HS + c] = hr;
-        hi[r * TC_HS + 32 + c] = hm;
-        lo[r * TC_HS + c] = bf16_bits(re - bf16_value(hr));
-        lo[r * TC_HS + 32 + c] = bf16_bits(im - bf16_value(hm));
-    }
-}
-
-// D = A . M for this warp; acc[mt][nt][i] is row 16 mt + gid (+8 for i >= 2),
-// column 8 nt + 2 tig (+1 for odd i).
-template <Dft D>
-__device__ __forceinline__ void tc_gemm(const unsigned char* buf, const unsigned char* tab, int lane,
-                                        float (&acc)[2][8][4]) {
-    const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
-    if (D == Dft::TF32) {
-        const uint32_t* A = reinterpret_cast<const uint32_t*>(buf);
-        const uint32_t* Bt = reinterpret_cast<const uint32_t*>(tab);
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-            const int k0 = 8 * ks;
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = 16 * mt + gid;
-                a[mt][0] = A[r * TC_AS + k0 + tig];
-                a[mt][1] = A[(r + 8) * TC_AS + k0 + tig];
-                a[mt][2] = A[r * TC_AS + k0 + tig + 4];
-                a[mt][3] = A[(r + 8) * TC_AS + k0 + tig + 4];
-            }
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const uint32_t b0 = Bt[(8 * nt + gid) * TC_AS + k0 + tig];
-                const uint32_t b1 = Bt[(8 * nt + gid) * TC_AS + k0 + tig + 4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][nt], a[mt], b0, b1);
-            }
-        }
-    } else {
-        const uint16_t* Ahi = reinterpret_cast<const uint16_t*>(buf);
-        const uint16_t* Alo = Ahi + 32 * TC_HS;
-        const uint16_t* Bhi = reinterpret_cast<const uint16_t*>(tab);
-        const uint16_t* Blo = Bhi + 64 * TC_HS;
-        auto pair = [](const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); };
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            const int k0 = 16 * ks;
-            uint32_t ah[2][4], al[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = 16 * mt + gid;
-                ah[mt][0] = pair(Ahi + r * TC_HS + k0 + 2 * tig);
-                ah[mt][1] = pair(Ahi + (r + 8) * TC_HS + k0 + 2 * tig);
-                ah[mt][2] = pair(Ahi + r * TC_HS + k0 + 2 * tig + 8);
-                ah[mt][3] = pair(Ahi + (r + 8) * TC_HS + k0 + 2 * tig + 8);
-                al[mt][0] = pair(Alo + r * TC_HS + k0 + 2 * tig);
-                al[mt][1] = pair(Alo + (r + 8) * TC_HS + k0 + 2 * tig);
-                al[mt][2] = pair(Alo + r * TC_HS + k0 + 2 * tig + 8);
-                al[mt][3] = pair(Alo + (r + 8) * TC_HS + k0 + 2 * tig + 8);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = (8 * nt + gid) * TC_HS + k0 + 2 * tig;
-                const uint32_t bh0 = pair(Bhi + col), bh1 = pair(Bhi + col + 8);
-                const uint32_t bl0 = pair(Blo + col), bl1 = pair(Blo + col + 8);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma_bf16(acc[mt][nt], al[mt], bh0, bh1);
-                    mma_bf16(acc[mt][nt], ah[mt], bl0, bl1);
-                    mma_bf16(acc[mt][nt], ah[mt], bh0, bh1);
-                }
-            }
-        }
-    }
-}
-
-// Forward 2-D DFT of z = zr + j zi (lane n holds column n) on tensor cores;
-// on return lane k holds Z[k][0..31].  buf: this warp's scratch (>= 9.2 KB).
-template <Dft D>
-__device__ __forceinline__ void tc_dft2(float (&zr)[S], float (&zi)[S], unsigned char* buf,
-                                        const unsigned char* tab, int lane) {
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][8][4];
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < S; ++m) tc_put<D>(buf, m, lane, zr[m], zi[m]);   // A[m][n] = z[m][n]
-    __syncwarp();
-    tc_gemm<D>(buf, tab, lane, acc);                                     // [Yr | Yi], Y = z F
-    __syncwarp();
-    // A2 = Y^T: row l, column m
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int m = 16 * mt + gid + ((i & 2) ? 8 : 0);
-                const int l = 8 * nt + 2 * tig + (i & 1);
-                tc_put<D>(buf, l, m, acc[mt][nt][i], acc[mt][nt + 4][i]);
-            }
-    __syncwarp();
-    tc_gemm<D>(buf, tab, lane, acc);                                     // [Re | Im] of Z^T
-    __syncwarp();
-    // Z[k][l] = D2[l][k] (re), D2[l][32 + k] (im): row k of Z to lane k
-    float2* zb = reinterpret_cast<float2*>(buf);
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int l = 16 * mt + gid + ((i & 2) ? 8 : 0);
-                const int k = 8 * nt + 2 * tig + (i & 1);
-                zb[k * TSTRIDE + l] = make_float2(acc[mt][nt][i], acc[mt][nt + 4][i]);
-            }
-    __syncwarp();
-#pragma unroll
-    for (int l = 0; l < S; ++l) {
-        const float2 v = zb[lane * TSTRIDE + l];
-        zr[l] = v.x;
-        zi[l] = v.y;
-    }
-    __syncwarp();
-}
+// The transform context of the SIMT path (no tensor-core state).
+struct NoTc {
+    __device__ void dft2(float (&)[32], float (&)[32], int) {}
+};
 
 // Row stride (in complex elements) of the stored W rows, chosen so that 32
 // lanes reading 32 different rows at one column hit distinct banks (128-bit
@@ -613,10 +416,10 @@ __device__ __forceinline__ unsigned load_support_reuse(const ImageArgs& a, const
 // known) lane k holds Z[k][0..31] = F2{z} row k in zr/zi; inv2alpha =
 // 1 / (2 alpha); swd: sum of w in FP64 (precision study only).  Wd: this
 // warp's scratch (the support tile and the transpose pass through it).
-template <typename T, Dft DFT, bool REUSE = false>
+template <typename T, Dft DFT, bool REUSE = false, class TC = NoTc>
 __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int x0, int lane,
                                                 const T* __restrict__ sw0,
-                                                typename Vec2<T>::type* Wd, const unsigned char* tctab,
+                                                typename Vec2<T>::type* Wd, TC* tc,
                                                 const unsigned char* tile,
                                                 T (&zr)[S], T (&zi)[S], BlockState<T>& st, T& inv2alpha_out,
                                                 double& swd_out, const ReuseCtx* ru = nullptr) {
@@ -677,7 +480,7 @@ __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int 
 
     if constexpr (DFT != Dft::SIMT) {
         // a3 on tensor cores (precision study); lane k ends with Z[k][0..31]
-        tc_dft2<DFT>(zr, zi, reinterpret_cast<unsigned char*>(Wd), tctab, lane);
+        tc->dft2(zr, zi, lane);
     } else {
         // a3: FFT over m (lane n holds column n)
         fft32<T>(zr, zi);
@@ -707,17 +510,17 @@ __device__ __forceinline__ bool transform_block(const ImageArgs& a, int y0, int 
 // a1-a3: load the support (lane n = column n), weight it, transform it.
 // On return (when some pixel is known) lane k holds Q[k][0..31] = F2{(f~-mu)w}
 // row k in zr/zi and the W rows are in Wd (layout of WRow<T>).
-template <typename T, int WS, Dft DFT, bool REUSE = false>
+template <typename T, int WS, Dft DFT, bool REUSE = false, class TC = NoTc>
 __device__ __forceinline__ bool prepare_block(const ImageArgs& a, int y0, int x0, int lane,
                                               const T* __restrict__ sw0,
-                                              typename Vec2<T>::type* Wd, const unsigned char* tctab,
+                                              typename Vec2<T>::type* Wd, TC* tc,
                                               const unsigned char* tile,
                                               T (&zr)[S], T (&zi)[S], BlockState<T>& st,
                                               const ReuseCtx* ru = nullptr) {
     using T2 = typename Vec2<T>::type;
     T inv2alpha;
     double swd;
-    if (!transform_block<T, DFT, REUSE>(a, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st, inv2alpha, swd, ru))
+    if (!transform_block<T, DFT, REUSE, TC>(a, y0, x0, lane, sw0, Wd, tc, tile, zr, zi, st, inv2alpha, swd, ru))
         return false;
 
     // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2,  W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha)
@@ -1002,26 +805,32 @@ __device__ __forceinline__ Pick argmax_pick(const float (&zr)[S], const float (&
     return pk;
 }
 
+// The picks of one block in iteration order (precision study): the
+// coefficient c = gamma p and the index u*S+v of every iteration.
+struct PickList {
+    float2* c;
+    int16_t* idx;
+};
+
 // a6 for the pick of iteration nu: c = gamma p, p = R[u,v] / W[0,0]
 // (Eqs. 10-11); records the index and adds Re(c e^{+j2pi(um+vn)/S}) to the
-// target pixels (sparse inverse of G).  DENSE (precision study): c is added
-// to the dense coefficient array gd[u][v] instead (G of Eq. 11 divided by
-// S^2), whose inverse transform runs on tensor cores after the loop.
+// target pixels (sparse inverse of G).  DENSE (precision study): the pick is
+// appended to the block's pick list instead; after the loop the list gives
+// the dense coefficient array (G of Eq. 11 divided by S^2), whose inverse
+// transform runs on tensor cores.
 template <int B, bool DENSE>
 __device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float invW0, int nu, int lane,
                                             int16_t* seq, const float2* __restrict__ scs,
                                             const int (&pm)[TargetPix<B>::P], const int (&pn)[TargetPix<B>::P],
-                                            float (&gacc)[TargetPix<B>::P], float2* gd, float& cr, float& ci,
-                                            bool pair = false) {
+                                            float (&gacc)[TargetPix<B>::P], const PickList* pl, float& cr,
+                                            float& ci, bool pair = false) {
     cr = gamma * (pk.Rr * invW0);
     ci = gamma * (pk.Ri * invW0);
     if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(pk.u * S + pk.v);
     if constexpr (DENSE) {
         if (lane == 0) {
-            float2 gv = gd[pk.u * S + pk.v];
-            gv.x += cr;
-            gv.y += ci;
-            gd[pk.u * S + pk.v] = gv;
+            pl->c[nu] = make_float2(cr, ci);
+            pl->idx[nu] = (int16_t)(pk.u * S + pk.v);
         }
     } else {
         // a conjugate pair adds Re(c e^{+j theta}) + Re(c* e^{-j theta}) = 2 Re(c e^{+j theta})
@@ -1042,7 +851,7 @@ template <int B, bool DENSE = false, bool CONJ = false>
 __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* Wd, float2* rowbuf,
                                         const float* __restrict__ swf, const float2* __restrict__ scs,
                                         const BlockState<float>& st, float gamma, int K, int L, int lane,
-                                        int16_t* seq, float (&gacc)[TargetPix<B>::P], float2* gd = nullptr) {
+                                        int16_t* seq, float (&gacc)[TargetPix<B>::P], const PickList* gd = nullptr) {
     constexpr int P = TargetPix<B>::P;
     if (K <= 0) return;
     float wfr[S / 2 + 1];
@@ -1222,39 +1031,6 @@ __device__ __forceinline__ void cta_tables(const MethodArgs& mth, T* sw0, T* swf
     }
 }
 
-// a9 on tensor cores (precision study): Re g = Re IDFT2(G) = Re DFT2(conj Gc)
-// with Gc = G / S^2 the summed coefficients c, evaluated densely by the same
-// two GEMM passes as the forward transform; the B x B target values are
-// gathered through shared memory into gacc (target pixel t of the block is
-// (L + t / B, L + t % B), L = (S - B) / 2).
-template <int B, Dft DFT, typename T>
-__device__ __forceinline__ void dense_inverse_targets(const float2* gd, typename Vec2<T>::type* Wd,
-                                                      typename Vec2<T>::type* rowbuf, const unsigned char* tctab,
-                                                      int lane, T (&zr)[S], T (&zi)[S],
-                                                      T (&gacc)[TargetPix<B>::P]) {
-    constexpr int LB = (S - B) / 2;
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < S; ++m) {   // lane n: column n of conj(Gc)
-        const float2 gv = gd[m * S + lane];
-        zr[m] = gv.x;
-        zi[m] = -gv.y;
-    }
-    tc_dft2<DFT>(zr, zi, reinterpret_cast<unsigned char*>(Wd), tctab, lane);   // lane k: row k
-    float* tb = reinterpret_cast<float*>(rowbuf);
-    if (lane >= LB && lane < LB + B) {
-#pragma unroll
-        for (int c = 0; c < B; ++c) tb[(lane - LB) * B + c] = zr[LB + c];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < TargetPix<B>::P; ++q) {
-        const int pidx = lane + 32 * q;
-        gacc[q] = pidx < B * B ? tb[pidx] : T(0);
-    }
-    __syncwarp();
-}
-
 // A support without a known pixel: no iterations (g = 0), the selection
 // sequence is -1, and the block is counted (reading: W[0][0] = 0).
 __device__ __forceinline__ void empty_block(int16_t* seq, int K, unsigned long long* empty) {
@@ -1266,12 +1042,12 @@ __device__ __forceinline__ void empty_block(int16_t* seq, int K, unsigned long l
 // Everything of one target block: a1-a3 (prepare), a4-a8 (iterate), a9.
 // With a tile context the support comes in by TMA; returns false when the
 // bounded wait for it gave up (the warp then stops taking blocks).
-template <typename T, int B, Dft DFT = Dft::SIMT, bool CONJ = false, bool REUSE = false>
+template <typename T, int B, bool CONJ = false, bool REUSE = false>
 __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk, int L, T gamma,
                                               const T* sw0, const T* swf, const typename Vec2<T>::type* scs,
                                               typename Vec2<T>::type* Wd, typename Vec2<T>::type* rowbuf,
-                                              const unsigned char* tctab, const TileReq& tr,
-                                              unsigned long long* empty, int lane, float delta = 0.f) {
+                                              const TileReq& tr, unsigned long long* empty, int lane,
+                                              float delta = 0.f) {
     constexpr int P = TargetPix<B>::P;
     const int by = (int)(blk / im.nbx);
     const int bx = (int)(blk - (long long)by * im.nbx);
@@ -1298,22 +1074,7 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
     for (int q = 0; q < P; ++q) gacc[q] = T(0);
 
     int16_t* seq = im.seq ? im.seq + (size_t)blk * im.K : nullptr;
-    if constexpr (DFT != Dft::SIMT) {
-        // precision study: dense coefficients of this block (warp's own 8 KB
-        // after the DFT table), inverse transform on tensor cores (a9)
-        float2* gd = reinterpret_cast<float2*>(const_cast<unsigned char*>(tctab) + TcTable<DFT>::bytes) +
-                     (threadIdx.x >> 5) * S * S;
-        float4* grow = reinterpret_cast<float4*>(gd + lane * S);
-#pragma unroll
-        for (int c = 0; c < S / 2; ++c) grow[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncwarp();
-        if (prepare_block<T, SmemLayout<T>::WS, DFT>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st)) {
-            iterate<B, true>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc, gd);
-            dense_inverse_targets<B, DFT>(gd, Wd, rowbuf, tctab, lane, zr, zi, gacc);
-        } else if (lane == 0) {
-            empty_block(seq, im.K, empty);
-        }
-    } else {
+    {
         ReuseCtx ru;
         if constexpr (REUSE) {
             ru.prev = im.out;
@@ -1322,8 +1083,8 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
             ru.bx = bx;
             ru.B = B;
         }
-        if (prepare_block<T, SmemLayout<T>::WS, DFT, REUSE>(im, y0, x0, lane, sw0, Wd, tctab, tile, zr, zi, st,
-                                                             REUSE ? &ru : nullptr)) {
+        if (prepare_block<T, SmemLayout<T>::WS, Dft::SIMT, REUSE>(im, y0, x0, lane, sw0, Wd, (NoTc*)nullptr, tile,
+                                                                   zr, zi, st, REUSE ? &ru : nullptr)) {
             iterate<B, false, CONJ>(zr, zi, Wd, rowbuf, swf, scs, st, gamma, im.K, L, lane, seq, gacc);
             __syncwarp();   // W area free for the next block
         } else if (lane == 0) {
@@ -1352,7 +1113,7 @@ __device__ __forceinline__ bool process_block(const ImageArgs& im, long long blk
 template <typename T, int WARPS> struct MinBlocks { static constexpr int value = 1; };
 template <int WARPS> struct MinBlocks<float, WARPS> { static constexpr int value = WARPS < 16 ? 16 / WARPS : 1; };
 
-template <typename T, int B, int WARPS, Dft DFT = Dft::SIMT>
+template <typename T, int B, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
 fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
     using T2 = typename Vec2<T>::type;
@@ -1366,9 +1127,7 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
     T2* Wd = reinterpret_cast<T2*>(smem + Lay::warp0_off + Lay::per_warp * warp);
     T2* rowbuf = Wd + Lay::w_elems;
 
-    unsigned char* tctab = smem + Lay::bytes(WARPS);   // tensor-core DFT table (precision study)
     cta_tables<T>(a.mth, sw0, swf, scs);
-    if constexpr (DFT != Dft::SIMT) tc_table<DFT>(tctab);
     __syncthreads();
 
     // tile copies need 128-byte aligned destinations (kept by the layout)
@@ -1394,8 +1153,7 @@ fsr_blocks_kernel(const __grid_constant__ KernelArgs a) {
         tr.bytes = kTileBytes + (unsigned)a.tx_extra;
         tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * wq);
         tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + wq;
-        if (!process_block<T, B, DFT>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tctab, tr, a.empty,
-                                      lane))
+        if (!process_block<T, B>(a.im, blk, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, tr, a.empty, lane))
             break;
     }
     // the last warp of the launch leaves the counter at zero for the next one
@@ -1463,8 +1221,8 @@ fsr_batch_kernel(const BatchArgs a) {
             tr.bytes = kTileBytes + (unsigned)a.tx_extra;
             tr.bar = smem_addr(smem + Lay::bar_off(WARPS) + 8 * warp);
             tr.parity = reinterpret_cast<uint32_t*>(smem + Lay::parity_off(WARPS)) + warp;
-            ok = process_block<T, B, Dft::SIMT, CONJ>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf,
-                                                      scs, Wd, rowbuf, nullptr, tr, a.empty, lane);
+            ok = process_block<T, B, CONJ>(im, item - __ldg(a.first + lo), a.mth.L, gamma, sw0, swf, scs, Wd,
+                                           rowbuf, tr, a.empty, lane);
         }
         if (!ok) break;   // a tile wait gave up: this warp takes no more blocks
         if constexpr (ONE_ROUND) break;
@@ -1507,8 +1265,8 @@ fsr_reuse_kernel(const __grid_constant__ ReuseLaunch a) {
     const int bx = a.t - a.slope * by;
     TileReq tr;
     tr.maps = nullptr;
-    process_block<T, B, Dft::SIMT, false, true>(a.im, (long long)by * a.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0,
-                                                swf, scs, Wd, rowbuf, nullptr, tr, a.empty, lane, a.delta);
+    process_block<T, B, false, true>(a.im, (long long)by * a.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0, swf, scs,
+                                     Wd, rowbuf, tr, a.empty, lane, a.delta);
 }
 
 }  // namespace fsrk

@@ -89,8 +89,8 @@ int check_method(fsr_handle* h, const fsr_params* p) {
     if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG && p->precision != FSR_TC_BF16X3 &&
         p->precision != FSR_TC_TF32)
         return fail(h, FSR_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
-    if ((p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32) && p->block != 4)
-        return fail(h, FSR_ERR_UNSUPPORTED, "tensor-core transform variants are built for B = 4 only");
+    if ((p->precision == FSR_TC_BF16X3 || p->precision == FSR_TC_TF32) && (p->block != 4 || p->iters > 256))
+        return fail(h, FSR_ERR_UNSUPPORTED, "tensor-core transform variants are built for B = 4 and K <= 256");
     if (p->update != FSR_UPDATE_SINGLE && p->update != FSR_UPDATE_CONJ_PAIR)
         return fail(h, FSR_ERR_INVALID_ARG, "update must be FSR_UPDATE_SINGLE or FSR_UPDATE_CONJ_PAIR");
     if (p->update == FSR_UPDATE_CONJ_PAIR &&
