@@ -422,7 +422,7 @@ def _measure_batch(fsr, handle, dev, torch):
             "graph": True}
 
 
-def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 4):
+def _measure_serving(fsr, handle, torch, seconds: float, streams: int = 2):
     """Poisson stream, mean 120 req/s: 720p/1080p/4K frames, quarter sampling or
     macroblock loss, K in {50, 100}, through the continuous-batching server."""
     from paper_2202_13926_gb300 import serving, synth
@@ -543,8 +543,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 48-image batch measurement")
     ap.add_argument("--no-k-sweep", action="store_true", help="skip the K = 100..400 sweep of the 1080p frame")
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
-                    help="length of the Poisson serving stream (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=16.0,
+                    help="length of the Poisson serving stream (0 = skip); 16 s puts ~600 requests in each class")
     ap.add_argument("--case", action="store_true",
                     help="run one configuration on the 1080p frame --repeat times, print the device times "
                          "and exit (the fixed workload of the profiler captures)")

@@ -160,10 +160,13 @@ void finish(fsr_server* s, Request* r, Clock::time_point now) {
 }
 
 // Launches up to kMaxBatch of the requests in q (taken from its front) as
-// one batch on the given free slot; the rest stay in q.  Returns false when
-// the launch table does not fit in the pool now (nothing launched).
+// one batch on the given free slot; the rest stay in q.  A long-class
+// request fills the GPU on its own, so the long class launches one request
+// at a time in arrival order: the earliest finishes first instead of every
+// request of a batch finishing with the batch's last block.  Returns false
+// when the launch table does not fit in the pool now (nothing launched).
 bool launch_on(fsr_server* s, int slot, std::vector<Request*>& q, bool long_class) {
-    const int n = (int)std::min<size_t>(q.size(), kMaxBatch);
+    const int n = (int)std::min<size_t>(q.size(), long_class ? 1 : kMaxBatch);
     Launch& L = s->launches[slot];
     size_t toff = 0;
     const size_t tbytes = fsri::table_bytes(n);
