@@ -162,6 +162,91 @@ __device__ __forceinline__ int wrap(int i) {
     else return i < 0 ? i + SZ : i;
 }
 
+// In-register radix-2 FFT of length N (a power of two <= 32), natural order
+// in and out, X[k] = sum_m x[m] e^{-j 2 pi k m / N}.
+template <int N, typename T>
+__device__ __forceinline__ void fft_pow2(T (&re)[N], T (&im)[N]) {
+    constexpr int LOG = N == 2 ? 1 : N == 4 ? 2 : N == 8 ? 3 : N == 16 ? 4 : 5;
+    T ar[N], ai[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 0; b < LOG; ++b) r |= ((i >> b) & 1) << (LOG - 1 - b);
+        ar[i] = re[r];
+        ai[i] = im[r];
+    }
+#pragma unroll
+    for (int half = 1; half < N; half *= 2) {
+#pragma unroll
+        for (int j = 0; j < N; j += 2 * half) {
+#pragma unroll
+            for (int t = 0; t < half; ++t) {
+                const int tw = t * (32 / (2 * half));   // e^{-j 2 pi tw / 32}
+                const T br = ar[j + t + half], bi = ai[j + t + half];
+                T xr, xi;
+                if (tw == 0) {
+                    xr = br; xi = bi;
+                } else if (tw == 8) {   // times -j
+                    xr = bi; xi = -br;
+                } else {
+                    const T c = T(cos_2pi32(tw)), sn = T(-sin_2pi32(tw));
+                    xr = br * c - bi * sn;
+                    xi = br * sn + bi * c;
+                }
+                ar[j + t + half] = ar[j + t] - xr;
+                ai[j + t + half] = ai[j + t] - xi;
+                ar[j + t] = ar[j + t] + xr;
+                ai[j + t] = ai[j + t] + xi;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        re[i] = ar[i];
+        im[i] = ai[i];
+    }
+}
+
+// In-register 24-point FFT, X[k] = sum_n x[n] e^{-j 2 pi k n / 24}, as
+// 3 x 8 (n = 3 n1 + n2, k = k1 + 8 k2): three 8-point FFTs over n1, the
+// twiddles e^{-j 2 pi n2 k1 / 24}, eight 3-point DFTs over n2.
+template <typename T>
+__device__ __forceinline__ void fft24(T (&re)[24], T (&im)[24]) {
+    T yr[3][8], yi[3][8];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            yr[n2][n1] = re[3 * n1 + n2];
+            yi[n2][n1] = im[3 * n1 + n2];
+        }
+        fft_pow2<8>(yr[n2], yi[n2]);
+    }
+    const T h = T(0.866025403784438646763723170752936183);   // sin(pi / 3)
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        // y1, y2 of this k1 times e^{-j 2 pi n2 k1 / 24}
+        T br = yr[1][k1], bi = yi[1][k1], cr = yr[2][k1], ci = yi[2][k1];
+        if (k1 != 0) {
+            const T c1 = T(cos_2pi24(k1)), s1 = T(-cos_2pi24(k1 - 6));
+            const T c2 = T(cos_2pi24(2 * k1)), s2 = T(-cos_2pi24(2 * k1 - 6));
+            const T tbr = br * c1 - bi * s1, tbi = br * s1 + bi * c1;
+            const T tcr = cr * c2 - ci * s2, tci = cr * s2 + ci * c2;
+            br = tbr; bi = tbi; cr = tcr; ci = tci;
+        }
+        const T ar = yr[0][k1], ai = yi[0][k1];
+        const T sr = br + cr, si = bi + ci, dr = br - cr, di = bi - ci;
+        const T tr = ar - T(0.5) * sr, ti = ai - T(0.5) * si;
+        re[k1] = ar + sr;
+        im[k1] = ai + si;
+        re[k1 + 8] = tr + h * di;    // a + w b + w^2 c, w = e^{-j 2 pi / 3}
+        im[k1 + 8] = ti - h * dr;
+        re[k1 + 16] = tr - h * di;
+        im[k1 + 16] = ti + h * dr;
+    }
+}
+
 // One block: a1-a9 for support size SZ, target B x B.
 template <typename T, int SZ, int B>
 __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L, T gamma, const T* sw0,
@@ -221,14 +306,97 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
             sfw += __shfl_xor_sync(FULL, sfw, o);
         }
         const T mu = sfw / sw;
+        constexpr bool FFT24 = SZ == 24 && sizeof(T) == 4;
+        unsigned dmax = 0;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
             const int i = lane + 32 * j;
             const int x = (i / SZ) * XS + i % SZ;
-            xs[x] = ws[x] > T(0) ? (xs[x] - mu) * ws[x] : T(0);
+            const bool kn = ws[x] > T(0);
+            const T d = xs[x] - mu;
+            xs[x] = kn ? d * ws[x] : T(0);
+            const unsigned ab = __float_as_uint((float)d) & 0x7fffffffu;
+            dmax = (kn && ab > dmax) ? ab : dmax;
         }
         __syncwarp();
+        T zr[P], zi[P], w0r = T(0);
 
+        if constexpr (FFT24) {
+            // ---- a3 as in the S = 32 kernel: one complex 2-D FFT of
+            //      z = x + j alpha w (alpha = 2^e >= max |f - mu|), rows then
+            //      columns, by lanes 0..23; Q and W separated with the
+            //      conjugate-symmetry identities (exactly Hermitian) ----
+            dmax = __reduce_max_sync(FULL, dmax);
+            unsigned aexp = (dmax >> 23) + 1u;
+            aexp = (dmax >= 0x00800000u && dmax < 0x7e000000u) ? aexp : 127u;
+            const T alpha = T(__uint_as_float(aexp << 23));
+            const T inv2alpha = T(__uint_as_float((253u - aexp) << 23));   // 1 / (2 alpha)
+            constexpr int FS = 25;   // row stride (T2) of the first-pass output: conflict-free rows and columns
+            T2* Yz = reinterpret_cast<T2*>(area) + SZ * WROW;   // in the second copy of the W rows
+            const int rl = lane < SZ ? lane : SZ - 1;            // lanes 24..31 repeat row / column 23
+            T fr[SZ], fi[SZ];
+#pragma unroll
+            for (int n = 0; n < SZ; ++n) {
+                fr[n] = xs[rl * XS + n];
+                fi[n] = ws[rl * XS + n] * alpha;
+            }
+            fft24(fr, fi);   // lane m: Y[m][l] = sum_n z[m][n] e^{-j 2 pi l n / 24}
+            if (lane < SZ) {
+#pragma unroll
+                for (int l = 0; l < SZ; ++l) Yz[lane * FS + l] = make_float2(fr[l], fi[l]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m < SZ; ++m) {
+                const T2 y = Yz[m * FS + rl];
+                fr[m] = y.x;
+                fi[m] = y.y;
+            }
+            fft24(fr, fi);   // lane l: Z[k][l], k = 0..23
+            __syncwarp();    // the first-pass output is read no more
+            // Q[k][l] = (Z[k][l] + conj Z[-k][-l]) / 2, W[k][l] = (Z[k][l] - conj Z[-k][-l]) / (2j alpha);
+            // Z[-k][-l] is register -k of the lane holding column -l
+            const int src = (SZ - rl) % SZ;
+            T2* Qt = Yz;   // Q goes through the same place to the lanes' patches
+#pragma unroll
+            for (int k = 0; k <= SZ / 2; ++k) {
+                const int k2 = (SZ - k) % SZ;
+                const T cr = __shfl_sync(FULL, fr[k2], src);
+                const T ci = __shfl_sync(FULL, fi[k2], src);
+                T dr = cr, di = ci;
+                if (k2 != k) {
+                    dr = __shfl_sync(FULL, fr[k], src);
+                    di = __shfl_sync(FULL, fi[k], src);
+                }
+                if (lane < SZ) {
+                    const T ar = fr[k], ai = fi[k];
+                    const T2 w1 = make_float2((ai + ci) * inv2alpha, (cr - ar) * inv2alpha);
+                    Wr[k * WROW + lane] = w1;
+                    if (lane < CP) Wr[k * WROW + SZ + lane] = w1;
+                    Qt[k * FS + lane] = make_float2((ar + cr) * T(0.5), (ai - ci) * T(0.5));
+                    if (k == 0 && lane == 0) w0r = w1.x;
+                    if (k2 != k) {
+                        const T br = fr[k2], bi = fi[k2];
+                        const T2 w2 = make_float2((bi + di) * inv2alpha, (dr - br) * inv2alpha);
+                        Wr[k2 * WROW + lane] = w2;
+                        if (lane < CP) Wr[k2 * WROW + SZ + lane] = w2;
+                        Qt[k2 * FS + lane] = make_float2((br + dr) * T(0.5), (bi - di) * T(0.5));
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < RP; ++r)
+#pragma unroll
+                for (int j = 0; j < CP; ++j) {
+                    const T2 q = Qt[(k0 + r) * FS + l0 + j];
+                    zr[r * CP + j] = q.x;
+                    zi[r * CP + j] = q.y;
+                }
+            __syncwarp();
+            // the second copy of the W rows (rows S .. 2S-1 repeat 0 .. S-1)
+            for (int e = lane; e < SZ * WROW; e += 32) Wr[SZ * WROW + e] = Wr[e];
+        } else {
         // ---- a3, pass 1 (over n): Y[m][l] = sum_n v[m][n] e^{-j 2 pi l n / S},
         //      for the rows m and columns l of this lane's patch ----
         if constexpr (RP == 1) {
@@ -294,7 +462,6 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         __syncwarp();
 
         // ---- a3, pass 2 (over m): Z[k][l] = sum_m Y[m][l] e^{-j 2 pi k m / S} ----
-        T zr[P], zi[P], w0r = T(0);
         {
             T2 wv[P];
 #pragma unroll
@@ -336,6 +503,7 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                 }
             if (lane == 0) w0r = wv[0].x;   // W[0][0] (component 0 of lane 0)
         }
+        }   // direct DFTs
         const T W0 = __shfl_sync(FULL, w0r, 0);
         __syncwarp();
 
