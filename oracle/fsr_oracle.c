@@ -183,6 +183,7 @@ int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
             if (o && o->pre) o->pre[nu] = 0.0;
             if (o && o->pim) o->pim[nu] = 0.0;
             if (o && o->margin) o->margin[nu] = 0.0;
+            if (o && o->margin_nc) o->margin_nc[nu] = 0.0;
             if (o && o->Rhre) memcpy(o->Rhre + (size_t)(nu + 1) * SS, Rre, sizeof(double) * SS);
             if (o && o->Rhim) memcpy(o->Rhim + (size_t)(nu + 1) * SS, Rim, sizeof(double) * SS);
             continue;
@@ -247,6 +248,7 @@ int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
             if (o && o->pre) o->pre[nu] = qre;
             if (o && o->pim) o->pim[nu] = qim;
             if (o && o->margin) o->margin[nu] = top > 0.0 ? (top - runner) / top : 0.0;
+            if (o && o->margin_nc) o->margin_nc[nu] = top > 0.0 ? (top - runner) / top : 0.0;
             if (o && o->Rhre) memcpy(o->Rhre + (size_t)(nu + 1) * SS, Rre, sizeof(double) * SS);
             if (o && o->Rhim) memcpy(o->Rhim + (size_t)(nu + 1) * SS, Rim, sizeof(double) * SS);
             continue;
@@ -265,6 +267,16 @@ int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
             }
         }
         const int u = idx / S, v = idx % S;
+        if (o && o->margin_nc) {   /* diagnostic: the runner-up other than the conjugate of (u,v) */
+            const int cj = ((S - u) % S) * S + (S - v) % S;
+            double second_nc = -1.0;
+            for (int i = 0; i < SS; ++i) {
+                if (i == idx || i == cj) continue;
+                const double ob = wf[i] * (Rre[i] * Rre[i] + Rim[i] * Rim[i]);
+                if (ob > second_nc) second_nc = ob;
+            }
+            o->margin_nc[nu] = best > 0.0 ? (best - second_nc) / best : 0.0;
+        }
 
         /* Eq. (10): p = R_w[u,v] / W[0,0]. */
         const double pre = Rre[idx] / W0, pim = Rim[idx] / W0;
@@ -354,7 +366,8 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                              int H, int Wd, int pitch, int B, int L,
                              const fsr_oracle_params *P, long nsel,
                              const long *block_ids, int nthreads,
-                             double *out_target, double *out_im, int *seq, double *margin)
+                             double *out_target, double *out_im, int *seq, double *margin,
+                             double *margin_nc)
 {
     if (!img || !mask || !P || !out_target || H <= 0 || Wd <= 0 || pitch < Wd ||
         B <= 0 || L < 0 || P->S != B + 2 * L || P->K < 0)
@@ -393,6 +406,7 @@ long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
         memset(&o, 0, sizeof o);
         o.seq = seq ? seq + s * K : NULL;
         o.margin = margin ? margin + s * K : NULL;
+        o.margin_nc = margin_nc ? margin_nc + s * K : NULL;
         o.gre = gre;
         o.gim = gim;      /* diagnostic: Im g (the model is complex, Eq. 11) */
         o.g_need = need;  /* only the target pixels are written back */

@@ -45,6 +45,9 @@ typedef struct {
     double *pre;      /* K projection coefficients p, Eq. (10) */
     double *pim;
     double *margin;   /* K relative gaps (best - second) / best of the objective */
+    double *margin_nc; /* K relative gaps (best - second) / best with the conjugate of the
+                          selected component left out of "second" (diagnostic: ties
+                          between components that are not a conjugate pair) */
     double *Rhre;     /* (K+1)*S*S residual spectrum before each iteration */
     double *Rhim;
     double *Gre;      /* S*S final model spectrum G, Eq. (11) */
@@ -83,14 +86,15 @@ int fsr_oracle_block_scaled(const fsr_oracle_params *P, const double *f,
  * out_target: nsel*B*B reconstructed target pixels (NaN outside the image).
  * out_im: optional nsel*B*B diagnostic, Im g at the unknown target pixels
  *         (0 at known ones, NaN outside the image); the output is Re g.
- * seq, margin: nsel*K each, optional.
+ * seq, margin, margin_nc: nsel*K each, optional.
  * nthreads: OpenMP threads (<= 0: library default).
  * Returns the number of blocks without any known pixel, or -1 on error. */
 long fsr_oracle_image_blocks(const float *img, const unsigned char *mask,
                              int H, int Wd, int pitch, int B, int L,
                              const fsr_oracle_params *P, long nsel,
                              const long *block_ids, int nthreads,
-                             double *out_target, double *out_im, int *seq, double *margin);
+                             double *out_target, double *out_im, int *seq, double *margin,
+                             double *margin_nc);
 
 /* Re-use of reconstructed pixels (the sequential form the paper leaves out,
  * Sec. II): blocks in raster order; unknown pixels of earlier blocks' targets

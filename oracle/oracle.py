@@ -59,7 +59,7 @@ _IP = ctypes.POINTER(ctypes.c_int)
 class _BlockOut(ctypes.Structure):
     _fields_ = [(n, _DP) for n in ("w", "R0re", "R0im", "Wre", "Wim")] + \
                [("seq", _IP)] + \
-               [(n, _DP) for n in ("pre", "pim", "margin", "Rhre", "Rhim",
+               [(n, _DP) for n in ("pre", "pim", "margin", "margin_nc", "Rhre", "Rhim",
                                    "Gre", "Gim", "gre", "gim")] + \
                [("g_need", ctypes.POINTER(ctypes.c_ubyte))]
 
@@ -92,7 +92,7 @@ class OracleLib:
             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ubyte),
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             ctypes.POINTER(_Params), ctypes.c_long, ctypes.POINTER(ctypes.c_long),
-            ctypes.c_int, _DP, _DP, _IP, _DP]
+            ctypes.c_int, _DP, _DP, _IP, _DP, _DP]
         lib.fsr_oracle_image_blocks.restype = ctypes.c_long
         lib.fsr_oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -148,8 +148,9 @@ class OracleLib:
         o = _BlockOut()
         for n, a in arrs.items():
             setattr(o, n, _dp(a))
+        margin_nc = np.empty(max(K, 1))
         o.seq = seq.ctypes.data_as(_IP)
-        o.pre, o.pim, o.margin = _dp(pre), _dp(pim), _dp(margin)
+        o.pre, o.pim, o.margin, o.margin_nc = _dp(pre), _dp(pim), _dp(margin), _dp(margin_nc)
         if history:
             Rhre = np.empty((K + 1, S, S)); Rhim = np.empty((K + 1, S, S))
             o.Rhre, o.Rhim = _dp(Rhre), _dp(Rhim)
@@ -164,7 +165,7 @@ class OracleLib:
         res = dict(
             w=arrs["w"], R0=arrs["R0re"] + 1j * arrs["R0im"],
             W=arrs["Wre"] + 1j * arrs["Wim"], seq=seq[:K].copy(),
-            p=(pre + 1j * pim)[:K].copy(), margin=margin[:K].copy(),
+            p=(pre + 1j * pim)[:K].copy(), margin=margin[:K].copy(), margin_nc=margin_nc[:K].copy(),
             G=arrs["Gre"] + 1j * arrs["Gim"], g=arrs["gre"] + 1j * arrs["gim"],
             skipped=bool(r == 1))
         if history:
@@ -197,17 +198,18 @@ class OracleLib:
         im_target = np.empty((n, B, B))
         seq = np.empty((n, max(K, 1)), np.int32)
         margin = np.empty((n, max(K, 1)))
+        margin_nc = np.empty((n, max(K, 1)))
         P = _Params(B + 2 * L, K, rho, gamma, int(bool(freq_weight)), int(bool(conj_pairs)))
         r = self.lib.fsr_oracle_image_blocks(
             img.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, Wd, Wd, B, L,
             ctypes.byref(P), n,
             ids.ctypes.data_as(ctypes.POINTER(ctypes.c_long)) if ids is not None else None,
-            int(threads), _dp(target), _dp(im_target), seq.ctypes.data_as(_IP), _dp(margin))
+            int(threads), _dp(target), _dp(im_target), seq.ctypes.data_as(_IP), _dp(margin), _dp(margin_nc))
         if r < 0:
             raise ValueError("oracle rejected the image arguments")
-        return dict(target=target, seq=seq[:, :K], margin=margin[:, :K], n_empty=int(r),
-                    block_ids=np.arange(n) if ids is None else ids, im_target=im_target)
+        return dict(target=target, seq=seq[:, :K], margin=margin[:, :K], margin_nc=margin_nc[:, :K],
+                    n_empty=int(r), block_ids=np.arange(n) if ids is None else ids, im_target=im_target)
 
 
     def fsr_image_reuse(self, img: np.ndarray, mask: np.ndarray, B: int = 4, L: int = 14,

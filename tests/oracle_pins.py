@@ -179,6 +179,12 @@ def pin_argmax_exhaustive(lib):
         for nu in range(K):
             obj = (wf if fw else 1.0) * np.abs(res["R_hist"][nu]) ** 2
             assert int(res["seq"][nu]) == int(np.argmax(obj)), (seed, nu)
+            # the diagnostic gap to the best component that is not the pick's conjugate
+            u, v = divmod(int(res["seq"][nu]), S)
+            rest = obj.copy()
+            rest[u, v] = rest[(-u) % S, (-v) % S] = -1.0
+            gap = (obj[u, v] - rest.max()) / obj[u, v]
+            assert abs(res["margin_nc"][nu] - gap) <= 1e-9, (seed, nu)
 
 
 def pin_energy_decrease(lib):

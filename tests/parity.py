@@ -17,6 +17,10 @@ GREY_TOL = 0.5
 FRAC_MIN = 0.999
 PSNR_TOL_DB = 0.01
 TIE_MARGIN = 1e-12
+# relative gap between the best component and the best one that is not its
+# conjugate below which FP32 arithmetic cannot tell the two apart (the FP32
+# spectrum carries a few units of 2^-24 relative error per iteration)
+FP32_NEAR_TIE = 3e-6
 
 
 def psnr(x, truth, mask=None):
@@ -57,4 +61,12 @@ def same_sequence_pixels(seq_gpu, seq_ref, H, W, B):
     same = np.all(np.asarray(seq_gpu).astype(np.int64) == np.asarray(seq_ref).astype(np.int64), axis=1)
     nbx, nby = -(-W // B), -(-H // B)
     blocks = same.reshape(nby, nbx)
+    return np.kron(blocks, np.ones((B, B), bool))[:H, :W]
+
+
+def block_pixels(flags, H, W, B):
+    """H x W booleans: the pixels of the target blocks whose flag is set
+    (flags in raster order of the blocks)."""
+    nbx, nby = -(-W // B), -(-H // B)
+    blocks = np.asarray(flags, bool).reshape(nby, nbx)
     return np.kron(blocks, np.ones((B, B), bool))[:H, :W]
