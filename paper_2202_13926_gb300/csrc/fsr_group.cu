@@ -30,8 +30,6 @@
 namespace fsrk {
 namespace {
 
-constexpr int kWarpsGroup = 8;
-
 template <int SZ>
 struct Grp {
     static_assert(SZ == 4 || SZ == 8 || SZ == 16, "group kernels cover S = 4, 8, 16");
@@ -379,11 +377,15 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     }
 }
 
-// CTAs per SM the register budget is set for: 16 warps per SM at S = 16
-// (<= 128 registers), 24 at S = 8 (<= 85), 32 at S = 4 (<= 64).  Measured on
-// the 1080p frame: S = 4 0.53 ms with 16 warps per SM, 0.39 ms with 32;
-// S = 8 0.91 ms with 16, 0.78 ms with 24 (32 spills registers).
-template <int SZ> constexpr int group_min_ctas() { return SZ == 4 ? 4 : SZ == 8 ? 3 : 2; }
+// Warps per CTA and CTAs per SM the register budget is set for: 20 warps
+// per SM at S = 16 (2 x 10, <= 96 registers, no spill), 32 at S = 8 (4 x 8,
+// <= 64, 36 bytes spilled) and at S = 4 (4 x 8, <= 64, no spill).  Measured
+// on the 1080p frame, K = 100: S = 4 0.53 ms with 16 warps per SM, 0.39 ms
+// with 32; S = 8 0.91 ms with 16, 0.745 ms with 24 (3 x 8), 0.722 ms with
+// 32; S = 16 2.07 ms with 16 (2 x 8), 1.93 ms with 20 (2 x 10 or 4 x 5),
+// 2.19 ms with 21 (3 x 7), 2.13 ms with 24 (2 x 12, 52 bytes spilled).
+template <int SZ> constexpr int group_warps() { return SZ == 16 ? 10 : 8; }
+template <int SZ> constexpr int group_min_ctas() { return SZ == 16 ? 2 : 4; }
 
 template <int SZ, int B, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_kernel(const BatchArgs a) {
@@ -455,19 +457,21 @@ __global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_ke
 
 template <int SZ, int B>
 cudaError_t configure_one() {
-    return cudaFuncSetAttribute(fsr_group_kernel<SZ, B, kWarpsGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Grp<SZ>::bytes(kWarpsGroup));
+    constexpr int W = group_warps<SZ>();
+    return cudaFuncSetAttribute(fsr_group_kernel<SZ, B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Grp<SZ>::bytes(W));
 }
 
 template <int SZ, int B>
 cudaError_t launch_one(const BatchArgs& a, int chunk, int sm_count, cudaStream_t stream) {
-    const size_t smem = Grp<SZ>::bytes(kWarpsGroup);
+    constexpr int W = group_warps<SZ>();
+    const size_t smem = Grp<SZ>::bytes(W);
     int grid = 0;
     const long long take = (long long)Grp<SZ>::BPW * chunk;
-    cudaError_t e = persistent_grid(fsr_group_kernel<SZ, B, kWarpsGroup>, kWarpsGroup, smem,
+    cudaError_t e = persistent_grid(fsr_group_kernel<SZ, B, W>, W, smem,
                                     (a.total + take - 1) / take, sm_count, &grid);
     if (e != cudaSuccess) return e;
-    fsr_group_kernel<SZ, B, kWarpsGroup><<<grid, kWarpsGroup * 32, smem, stream>>>(a);
+    fsr_group_kernel<SZ, B, W><<<grid, W * 32, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

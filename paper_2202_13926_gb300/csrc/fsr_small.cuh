@@ -110,11 +110,11 @@ struct Layout {
 };
 
 // Warps per CTA: 8; FP64 at S = 24 takes 4 (shared memory per warp).  FP32
-// at S = 24 runs two CTAs per SM (at most 128 registers).
+// at S = 24 runs one CTA of 20 warps per SM (at most 96 registers; 220 KB of
+// shared memory): 1080p, K = 100, B = 4: 4.52 ms with 2 CTAs x 8 warps (at
+// most 128 registers), 4.31 ms with 18 warps, 4.20 ms with 20.
 template <typename T, int SZ>
-constexpr int warps() { return (sizeof(T) == 8 && SZ == 24) ? 4 : 8; }
-template <typename T, int SZ>
-constexpr int min_ctas() { return (sizeof(T) == 4 && SZ == 24) ? 2 : 1; }
+constexpr int warps() { return (sizeof(T) == 8 && SZ == 24) ? 4 : (SZ == 24 ? 20 : 8); }
 
 template <typename T, int SZ>
 __device__ __forceinline__ void tables(const MethodArgs& mth, T* sw0, T* swf, typename Vec2<T>::type* stw,
@@ -791,21 +791,16 @@ __device__ __forceinline__ void run(const BatchArgs& a) {
     }
 }
 
-// One CTA per SM at most by launch bounds (the register count is the
-// compiler's), and the two-CTA form (at most 128 registers) for FP32 S = 24.
+// One CTA per SM by launch bounds (the register count is the compiler's,
+// at most 65536 / (32 WARPS)).
 template <typename T, int SZ, int B, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) fsr_small_kernel(const BatchArgs a) {
-    run<T, SZ, B>(a);
-}
-template <typename T, int SZ, int B, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 2) fsr_small_kernel_2cta(const BatchArgs a) {
     run<T, SZ, B>(a);
 }
 
 template <typename T, int SZ, int B>
 constexpr auto kernel_of() {
-    if constexpr (min_ctas<T, SZ>() == 2) return fsr_small_kernel_2cta<T, SZ, B, warps<T, SZ>()>;
-    else return fsr_small_kernel<T, SZ, B, warps<T, SZ>()>;
+    return fsr_small_kernel<T, SZ, B, warps<T, SZ>()>;
 }
 
 template <typename T, int SZ, int B>
