@@ -349,17 +349,13 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
             }
         }
     };
-    // the loops run to the largest K of the warp (uniform).  S = 4, 8: a DC
-    // loop, then a loop without the split branches (S = 4 0.385 -> 0.365 ms,
-    // S = 8 0.776 -> 0.747 ms per 1080p frame); S = 16 keeps one loop (two
-    // copies of its larger body measured 2.07 -> 2.15 ms).
-    if constexpr (SZ < 16) {
-        int nu = 0;
-        while (nu < Kmax && __any_sync(FULL, split && active && nu < Kh)) step(nu++, true);
-        for (; nu < Kmax; ++nu) step(nu, false);
-    } else {
-        for (int nu = 0; nu < Kmax; ++nu) step(nu, true);
-    }
+    // the loops run to the largest K of the warp (uniform): a DC loop, then a
+    // loop without the split branches (1080p frame: S = 4 0.385 -> 0.365 ms,
+    // S = 8 0.776 -> 0.747 ms; S = 16 at 20 warps per SM 1.935 -> 1.922 ms,
+    // at 16 warps and 123 registers 2.07 -> 2.15 ms)
+    int nu = 0;
+    while (nu < Kmax && __any_sync(FULL, split && active && nu < Kh)) step(nu++, true);
+    for (; nu < Kmax; ++nu) step(nu, false);
 
 
     // ---- a9: write-back of the B x B target ----

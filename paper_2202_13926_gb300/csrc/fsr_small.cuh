@@ -513,6 +513,9 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         for (int r = 0; r < RP; ++r)
 #pragma unroll
             for (int j = 0; j < CP; ++j) wfv[r * CP + j] = swf[(k0 + r) * SZ + l0 + j];
+        // the published entry lane t < P examines, and its w_f offset within the patch
+        const int lane_pub = lane < P ? lane : P - 1;
+        const int lane_wf = (lane_pub / CP) * SZ + lane_pub % CP;
         int pm[PT], pn[PT];
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
@@ -716,13 +719,8 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
                     }
                     __syncwarp();
                     const int kw = (ul / (SZ / CP)) * RP, lw = (ul % (SZ / CP)) * CP;
-                    T2 rv;
-                    rv.x = rv.y = T(0);
-                    bool hit = false;
-                    if (lane < P) {
-                        rv = pub[lane];
-                        hit = objective<T>(rv.x, rv.y, swf[(kw + lane / CP) * SZ + lw + lane % CP]) == Mx;
-                    }
+                    const T2 rv = pub[lane_pub];
+                    const bool hit = lane < P && objective<T>(rv.x, rv.y, swf[kw * SZ + lw + lane_wf]) == Mx;
                     int pf = __ffs(__ballot_sync(FULL, hit)) - 1;
                     if (pf < 0) pf = 0;   // unreachable: the lane's maximum is one of its objectives
                     sr = __shfl_sync(FULL, rv.x, pf);
