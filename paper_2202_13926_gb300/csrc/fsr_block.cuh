@@ -813,19 +813,21 @@ struct PickList {
 };
 
 // a6 for the pick of iteration nu: c = gamma p, p = R[u,v] / W[0,0]
-// (Eqs. 10-11); records the index and adds Re(c e^{+j2pi(um+vn)/S}) to the
+// (Eqs. 10-11), formed as R[u,v] (gamma / W[0,0]) with the block constant
+// cg = gamma / W[0,0] (the same rounding as gamma (R / W[0,0]) when gamma is
+// a power of two); records the index and adds Re(c e^{+j2pi(um+vn)/S}) to the
 // target pixels (sparse inverse of G).  DENSE (precision study): the pick is
 // appended to the block's pick list instead; after the loop the list gives
 // the dense coefficient array (G of Eq. 11 divided by S^2), whose inverse
 // transform runs on tensor cores.
 template <int B, bool DENSE>
-__device__ __forceinline__ void record_pick(const Pick& pk, float gamma, float invW0, int nu, int lane,
+__device__ __forceinline__ void record_pick(const Pick& pk, float cg, int nu, int lane,
                                             int16_t* seq, const float2* __restrict__ scs,
                                             const int (&pm)[TargetPix<B>::P], const int (&pn)[TargetPix<B>::P],
                                             float (&gacc)[TargetPix<B>::P], const PickList* pl, float& cr,
                                             float& ci, bool pair = false) {
-    cr = gamma * (pk.Rr * invW0);
-    ci = gamma * (pk.Ri * invW0);
+    cr = pk.Rr * cg;
+    ci = pk.Ri * cg;
     if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(pk.u * S + pk.v);
     if constexpr (DENSE) {
         if (lane == 0) {
@@ -863,7 +865,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
         pm[q] = L + (lane + 32 * q) / B;
         pn[q] = L + (lane + 32 * q) % B;
     }
-    const float invW0 = 1.f / st.W0;
+    const float cg = gamma * (1.f / st.W0);
     const float2* wrow_k = Wd + lane * WS32;
     float g[NG];
     float cr, ci;
@@ -876,7 +878,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
         pass_split_objective(zr, zi, wfr, wrow_k, ar, ai, g);
         for (;;) {
             pk = argmax_pick<true>(zr, zi, g, Wd, rowbuf, swf, ar, ai, lane);
-            record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
+            record_pick<B, DENSE>(pk, cg, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
                                   CONJ && !self_conjugate(pk.u, pk.v));
             if (++nu == K) return;
             if ((pk.u | pk.v) != 0) break;
@@ -900,7 +902,7 @@ __device__ __forceinline__ void iterate(float (&zr)[S], float (&zi)[S], float2* 
             else pass_update<false>(zr, zi, wfr, row, s, cr, ci, g);
         }
         pk = argmax_pick<false>(zr, zi, g, Wd, rowbuf, swf, 0.f, 0.f, lane);
-        record_pick<B, DENSE>(pk, gamma, invW0, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
+        record_pick<B, DENSE>(pk, cg, nu, lane, seq, scs, pm, pn, gacc, gd, cr, ci,
                               CONJ && !self_conjugate(pk.u, pk.v));
         if (++nu == K) return;
     }

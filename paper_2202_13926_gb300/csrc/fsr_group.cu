@@ -278,7 +278,7 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     const int Kh = valid ? im.K : 0;
     int16_t* seq = (valid && im.seq) ? im.seq + (size_t)blk * im.K : nullptr;
     if (valid && !active && t == 0) empty_block(seq, im.K, empty);
-    const float invW0 = active ? 1.f / W0 : 0.f;
+    const float cg = active ? gamma * (1.f / W0) : 0.f;   // c = R[u,v] gamma / W[0,0] (Eqs. 10, 11)
     bool split = true;             // R = a W + Q (DC phase)
     float ar = mu, ai = 0.f;
     float m_lane = (active && Kh > 0) ? split_objective_row<SZ>(zr, zi, wfr, Wd + t * WS, ar, ai) : 0.f;
@@ -312,7 +312,7 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
         const float Ri = __shfl_sync(FULL, ri, gb + v);
 
         // a6 (Eqs. 10, 11): c = gamma p, the target pixels of the sparse inverse
-        const float cr = gamma * (Rr * invW0), ci = gamma * (Ri * invW0);
+        const float cr = Rr * cg, ci = Ri * cg;
         if (run) {
             if (seq != nullptr && t == 0) seq[nu] = (int16_t)(u * SZ + v);
 #pragma unroll

@@ -523,6 +523,7 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
             pn[q] = L + (lane + 32 * q) % B;
         }
         const T invW0 = T(1) / W0;
+        const T cg = gamma * invW0;   // FP32: c = R[u,v] gamma / W[0,0] (Eqs. 10, 11)
         T o[P];
         int nu = 0;
         T cr = T(0), ci = T(0);
@@ -611,8 +612,13 @@ __device__ __forceinline__ void block(const ImageArgs& im, long long blk, int L,
         };
         // a6 for the picked component: c, the recorded index, the target pixels.
         auto apply = [&]() {
-            cr = gamma * (sr * invW0);
-            ci = gamma * (si * invW0);
+            if constexpr (sizeof(T) == 4) {
+                cr = sr * cg;
+                ci = si * cg;
+            } else {   // FP64 debug: gamma (R / W[0,0]) in the oracle's order
+                cr = gamma * (sr * invW0);
+                ci = gamma * (si * invW0);
+            }
             if (seq != nullptr && lane == 0) seq[nu] = (int16_t)(u * SZ + v);
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
