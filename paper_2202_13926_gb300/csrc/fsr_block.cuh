@@ -1261,6 +1261,12 @@ fsr_reuse_kernel(const __grid_constant__ ReuseLaunch a) {
     T2* rowbuf = Wd + Lay::w_elems;
     cta_tables<T>(a.mth, sw0, swf, scs);
     __syncthreads();
+    // Launched as a programmatic dependent of the previous wavefront: the
+    // tables above overlap its end; nothing of the image or the output is
+    // read before it has completed and its writes are visible.  The next
+    // wavefront may then start its own tables.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int j = blockIdx.x * WARPS + warp;
     if (j >= a.count) return;
     const int by = a.by_lo + j;
