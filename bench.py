@@ -27,6 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 H, W, B, L, K_ITERS, RHO, GAMMA = 1080, 1920, 4, 14, 100, 0.7, 0.5
+# rho-hat as fsr_params carries it (binary32); the oracle legs use the same value
+RHO_ABI = float(np.float32(RHO))
 IMG_SEED = 2
 METRIC = "megapixels/s and 1080p fps at K=100 within oracle tolerance; p50/p99 serving latency"
 SMEM_BYTES_PER_CLK_SM = 128          # shared-memory bandwidth per SM per clock
@@ -183,7 +185,7 @@ def _oracle_sample(img, mask, rows, threads):
     nbx = -(-W // B)
     ids = np.concatenate([np.arange(r * nbx, (r + 1) * nbx) for r in rows])
     t0 = time.perf_counter()
-    res = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K_ITERS, rho=RHO, gamma=GAMMA,
+    res = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K_ITERS, rho=RHO_ABI, gamma=GAMMA,
                                   block_ids=ids, threads=threads)
     return res, ids, time.perf_counter() - t0
 
@@ -347,7 +349,7 @@ def _measure_reuse(fsr, handle, img, mask, d_img, d_mask, d_out, stream, flush, 
             oracle.build()
             got = d_out.cpu().numpy().astype(np.float64)
             nb = check_rows * nbx
-            ref = oracle.fsr_image_reuse(img, mask, B=B, L=L, K=K_ITERS, delta=delta, rho=RHO, gamma=GAMMA,
+            ref = oracle.fsr_image_reuse(img, mask, B=B, L=L, K=K_ITERS, delta=delta, rho=RHO_ABI, gamma=GAMMA,
                                          nblocks=nb, given=got)["out"]
             part = slice(0, check_rows * B)
             unk = mask[part] == 0

@@ -17,6 +17,12 @@ GREY_TOL = 0.5
 FRAC_MIN = 0.999
 PSNR_TOL_DB = 0.01
 TIE_MARGIN = 1e-12
+# rho-hat as the library receives it: fsr_params carries it as a binary32
+# (0.7 -> 0.699999988...); the oracle is given the same value, so that both
+# compute the spatial weights of Eq. (5) from one parameter (with rho = 0.7
+# in binary64 the weights differ by up to ~4e-7 relative, enough to swap two
+# objectives 4e-8 apart)
+RHO = float(np.float32(0.7))
 # relative gap between the best component and the best one that is not its
 # conjugate below which FP32 arithmetic cannot tell the two apart (the FP32
 # spectrum carries a few units of 2^-24 relative error per iteration)

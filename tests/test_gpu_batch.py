@@ -191,7 +191,7 @@ def test_mixed_batch_48_images_full_size(fsr_mod, handle):
         H, W = it["img"].shape
         nbx, nby = -(-W // 4), -(-H // 4)
         ids = np.unique(np.concatenate([[0, nbx * nby - 1], rng.choice(nbx * nby, 100, replace=False)]))
-        r = oracle.fsr_image_blocks(it["img"], it["mask"], K=it["K"], block_ids=ids)
+        r = oracle.fsr_image_blocks(it["img"], it["mask"], K=it["K"], block_ids=ids, rho=PA.RHO)
         out = it["d_out"].cpu().numpy()
         assert np.array_equal(out[it["mask"] == 1], it["img"][it["mask"] == 1])
         for s, b in enumerate(ids):
@@ -243,7 +243,7 @@ def test_multichannel_frame_matches_the_oracle(fsr_mod, handle, per_channel_mask
     got = out.cpu().numpy().astype(np.float64)
     for c in range(3):
         m = masks[c] if per_channel_masks else masks
-        r = oracle.fsr_image_blocks(planes[c], m, K=K)
+        r = oracle.fsr_image_blocks(planes[c], m, K=K, rho=PA.RHO)
         ref = oracle.assemble_image(r["target"], H, W, 4)
         assert np.array_equal(got[c][m == 1], planes[c][m == 1].astype(np.float64)), c
         assert PA.frac_within(got[c], ref) >= PA.FRAC_MIN, c

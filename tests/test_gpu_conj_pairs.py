@@ -45,7 +45,7 @@ def _run(handle, img, mask, K, precision="fp32", seq=False):
 
 
 def _oracle(img, mask, K, threads=0):
-    r = oracle.fsr_image_blocks(img, mask, B=4, L=14, K=K, conj_pairs=True, threads=threads)
+    r = oracle.fsr_image_blocks(img, mask, B=4, L=14, K=K, conj_pairs=True, threads=threads, rho=PA.RHO)
     return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], 4), r
 
 

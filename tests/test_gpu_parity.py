@@ -45,6 +45,7 @@ def run_gpu(h, img, mask, **kw):
 
 def run_oracle(img, mask, B=4, K=100, **kw):
     L = (32 - B) // 2
+    kw.setdefault("rho", PA.RHO)
     r = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K, **kw)
     return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B), r
 
@@ -211,7 +212,7 @@ def test_empty_blocks_are_counted_like_the_oracle(handle):
     H, W = 100, 140
     img = synth.sinusoid_image(H, W, seed=41)
     m = synth.macroblock_mask(H, W, seed=42, lost=0.6, mb=40)
-    n_ref = oracle.fsr_image_blocks(img, m, K=10)["n_empty"]
+    n_ref = oracle.fsr_image_blocks(img, m, K=10, rho=PA.RHO)["n_empty"]
     assert n_ref > 0
     fsr.fsr_empty_blocks(handle.ptr)                       # reset
     for prec in ("fp32", "fp64"):

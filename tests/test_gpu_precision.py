@@ -86,7 +86,7 @@ def test_precision_study_on_1080p_quarter_sampling(handle):
     """The 1080p quarter-sampling frame in FP32-SIMT, BF16x3 and TF32 transform
     modes; each against the FP64 oracle (whole frame)."""
     img, mask = synth.fhd_quarter_case()
-    r = oracle.fsr_image_blocks(img, mask, K=100)
+    r = oracle.fsr_image_blocks(img, mask, K=100, rho=PA.RHO)
     ref = oracle.assemble_image(r["target"], 1080, 1920, 4)
     rows = {}
     for mode in MODES:

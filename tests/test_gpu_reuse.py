@@ -68,7 +68,7 @@ def _run(handle, img, mask, B=4, K=100, delta=DELTA, precision="fp32", seq=False
 
 
 def _oracle(img, mask, B=4, K=100, delta=DELTA, given=None):
-    return oracle.fsr_image_reuse(img, mask, B=B, L=(32 - B) // 2, K=K, delta=delta, given=given)
+    return oracle.fsr_image_reuse(img, mask, B=B, L=(32 - B) // 2, K=K, delta=delta, given=given, rho=PA.RHO)
 
 
 def _fp32_check(got, img, mask, B=4, K=100, delta=DELTA, seq_ref=None):

@@ -45,7 +45,7 @@ def _frames(specs, seed):
 def _oracle_image(img, mask, K, support=32, B=4):
     img = np.asarray(img, np.float32)
     mask = np.asarray(mask, np.uint8)
-    r = oracle.fsr_image_blocks(img, mask, B=B, L=(support - B) // 2, K=K)
+    r = oracle.fsr_image_blocks(img, mask, B=B, L=(support - B) // 2, K=K, rho=PA.RHO)
     return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B)
 
 

@@ -47,7 +47,7 @@ def _run(handle, img, mask, S, B, K, precision="fp32", seq=False):
 
 
 def _oracle(img, mask, S, B, K):
-    r = oracle.fsr_image_blocks(img, mask, B=B, L=(S - B) // 2, K=K)
+    r = oracle.fsr_image_blocks(img, mask, B=B, L=(S - B) // 2, K=K, rho=PA.RHO)
     return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B), r
 
 

@@ -88,7 +88,7 @@ def test_tile_copies_match_the_oracle_at_image_edges(fsr_mod, handle):
     img = synth.sinusoid_image(H, W, seed=21)
     mask = synth.iid_mask(H, W, seed=22, missing=0.5)
     got, seq = _run(fsr_mod, handle, img, mask, 96, iters=40, precision="fp64")
-    r = oracle.fsr_image_blocks(img, mask, K=40)
+    r = oracle.fsr_image_blocks(img, mask, K=40, rho=PA.RHO)
     ref = oracle.assemble_image(r["target"], H, W, 4)
     n_hard, _ = PA.sequence_mismatches(seq.reshape(-1, 40), r["seq"], r["margin"])
     assert n_hard == 0
