@@ -44,7 +44,7 @@ def run_gpu(h, img, mask, **kw):
 
 
 def run_oracle(img, mask, B=4, K=100, **kw):
-    L = (32 - B) // 2
+    L = kw.pop("L", (32 - B) // 2)
     kw.setdefault("rho", PA.RHO)
     r = oracle.fsr_image_blocks(img, mask, B=B, L=L, K=K, **kw)
     return oracle.assemble_image(r["target"], img.shape[0], img.shape[1], B), r
@@ -95,21 +95,23 @@ def test_ragged_sizes(handle, H, W, B, K):
             assert n_out <= max(1, int((1 - PA.FRAC_MIN) * got.size)), n_out
 
 
+@pytest.mark.parametrize("S", [32, 24, 16, 8])
 @pytest.mark.parametrize("H,W", [(40, 16384), (16384, 40), (3, 20000)])
-def test_extreme_aspect_ratios(handle, H, W):
+def test_extreme_aspect_ratios(handle, H, W, S):
     """Very wide and very tall images (block coordinates and tile copies far
     from the origin along one axis, one or two block rows or columns in the
-    other) against the oracle: FP32 within the acceptance bar, FP64 with the
-    oracle's sequences up to the tie class."""
+    other) against the oracle, for the kernels of every support size but 4:
+    FP32 within the acceptance bar, FP64 with the oracle's sequences up to
+    the tie class."""
     img = synth.pink_image(H, W, seed=H + W)
     mask = synth.quarter_mask(H, W, seed=H * 7 + W)
-    K = 20
-    ref, r = run_oracle(img, mask, K=K)
-    got = run_gpu(handle, img, mask, iters=K)
+    K, L = 20, (S - 4) // 2
+    ref, r = run_oracle(img, mask, K=K, L=L)
+    got = run_gpu(handle, img, mask, iters=K, border=L)
     assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
     assert PA.frac_within(got, ref) >= PA.FRAC_MIN
     assert abs(PA.psnr(got, img) - PA.psnr(ref, img)) <= PA.PSNR_TOL_DB
-    got, seq = run_gpu(handle, img, mask, iters=K, precision="fp64", seq=True)
+    got, seq = run_gpu(handle, img, mask, iters=K, border=L, precision="fp64", seq=True)
     n_hard, _ = PA.sequence_mismatches(seq, r["seq"], r["margin"])
     assert n_hard == 0
 
