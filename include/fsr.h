@@ -101,7 +101,9 @@ typedef struct fsr_params {
                          block's target takes part in later supports with its
                          reconstruction and the weight delta * rho^dist of Eq. (5).
                          Runs as one launch per wavefront of blocks (t = a*by + bx,
-                         a = ceil(L/B) + 1); single-image entry points, S = 32,
+                         a = ceil(L/B) + 1); fsr_reconstruct, fsr_reconstruct_host and
+                         fsr_reconstruct_batch (each image its own raster order, the
+                         images sharing the wavefront launches), S = 32,
                          FSR_UPDATE_SINGLE, FSR_FP32 / FSR_FP64_DEBUG only. */
 } fsr_params;
 
@@ -217,13 +219,18 @@ typedef struct fsr_batch fsr_batch;
  * p->seq_out are ignored (per image in d).  The work table lives in
  * handle-owned device memory: a call waits on the host until the previous
  * fsr_reconstruct_batch of this handle has finished before reusing it.
+ * With p->reuse > 0 the images run in the re-use form instead: one launch per
+ * wavefront index t holds wavefront t of every image that has one (up to 48
+ * images per launch), no work table; each image's output equals its
+ * single-image fsr_reconstruct bit for bit.
  * Errors: as fsr_reconstruct, for every image; OOM for the table. */
 int fsr_reconstruct_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p, void *stream);
 
 /* Prepare a reusable batch: validates the images, uploads the work table to
  * device memory owned by the batch and captures the launch (counter reset +
  * kernel) in a CUDA graph, with the handle's current schedule.  The image
- * buffers must stay valid while the batch is used.  Synchronous. */
+ * buffers must stay valid while the batch is used.  Synchronous.
+ * UNSUPPORTED for p->reuse > 0 (plans run independent blocks). */
 int fsr_batch_create(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p, fsr_batch **out);
 
 /* Replay the captured launch on `stream` (asynchronous).  Launches of one
@@ -238,7 +245,8 @@ int fsr_batch_destroy(fsr_batch *b);
  * batch (its outputs are written), keep the fastest for (p->block,
  * p->precision) in the handle and, if the handle has a schedule cache path,
  * store it there.  best / best_ms may be NULL.  Synchronous.  The outputs of
- * every schedule are identical, so the choice only affects time. */
+ * every schedule are identical, so the choice only affects time.
+ * UNSUPPORTED for p->reuse > 0. */
 int fsr_autotune_batch(fsr_handle *h, int n, const fsr_image_desc *d, const fsr_params *p,
                        fsr_schedule *best, float *best_ms);
 

@@ -1236,15 +1236,24 @@ fsr_batch_kernel(const BatchArgs a) {
 // block of the raster order before it whose target meets its support (rows
 // by - ceil(L/B) .. by, columns up to bx + ceil(L/B)) ran in an earlier
 // launch, and no two blocks of one launch touch each other's supports.
-struct ReuseLaunch {
+// One image's blocks on wavefront t: block rows by_lo .. by_lo + count - 1
+// (bx = t - a by); they are the launch's blocks first .. first + count - 1.
+struct ReuseSeg {
     ImageArgs im;
+    int by_lo, count, first;
+};
+constexpr int kReuseSegs = 48;   // images per launch (the launch parameters stay below 4 KB)
+
+struct ReuseLaunch {
     MethodArgs mth;
     float delta;            // re-use weight (0 < delta <= 1)
     int t;                  // wavefront
     int slope;              // a = ceil(L / B) + 1
-    int by_lo, count;       // blocks by_lo .. by_lo + count - 1 (by), bx = t - a by
+    int nseg, total;        // segments, and the blocks they hold
     unsigned long long* empty;
+    ReuseSeg seg[kReuseSegs];
 };
+static_assert(sizeof(ReuseLaunch) <= 4096, "re-use launch parameters must fit the 4 KB parameter space");
 
 template <typename T, int B, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
@@ -1268,12 +1277,15 @@ fsr_reuse_kernel(const __grid_constant__ ReuseLaunch a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int j = blockIdx.x * WARPS + warp;
-    if (j >= a.count) return;
-    const int by = a.by_lo + j;
+    if (j >= a.total) return;
+    int s = 0;   // the segment (image) of block j
+    while (s + 1 < a.nseg && a.seg[s + 1].first <= j) ++s;
+    const ReuseSeg& sg = a.seg[s];
+    const int by = sg.by_lo + (j - sg.first);
     const int bx = a.t - a.slope * by;
     TileReq tr;
     tr.maps = nullptr;
-    process_block<T, B, false, true>(a.im, (long long)by * a.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0, swf, scs,
+    process_block<T, B, false, true>(sg.im, (long long)by * sg.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0, swf, scs,
                                      Wd, rowbuf, tr, a.empty, lane, a.delta);
 }
 

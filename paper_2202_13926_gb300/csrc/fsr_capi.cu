@@ -257,31 +257,61 @@ int enqueue_single_fp32(fsr_handle* h, const float* img, const uint8_t* mask, in
 
 // Re-use form: one launch per wavefront t = a*by + bx (a = ceil(L/B) + 1) of
 // the raster order; block (by, bx) of launch t reads the targets of the
-// launches before it.
-int enqueue_reuse(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
-                  const fsr_params* p, float* out, cudaStream_t stream) {
+// launches before it.  The images of a batch have independent raster orders
+// and share the launches: launch t holds wavefront t of every image that has
+// one (up to kReuseSegs images per launch; more images take more launches
+// for the same t).
+int enqueue_reuse_images(fsr_handle* h, int n, const fsrk::ImageArgs* ims, const fsr_params* p,
+                         cudaStream_t stream) {
     fsrk::ReuseLaunch a;
     std::memset(&a, 0, sizeof a);
-    a.im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
     a.mth = method_args(p);
     a.delta = p->reuse;
     a.slope = (p->border + p->block - 1) / p->block + 1;
     a.empty = h->d_empty;
-    const int nbx = a.im.nbx, nby = (height + p->block - 1) / p->block;
-    const long long waves = (long long)a.slope * (nby - 1) + nbx;
-    for (long long t = 0; t < waves; ++t) {
-        // blocks with a*by + bx = t, 0 <= bx < nbx, 0 <= by < nby
-        const long long lo_num = t - (nbx - 1);
-        const long long by_lo = lo_num <= 0 ? 0 : (lo_num + a.slope - 1) / a.slope;
-        const long long by_hi = std::min<long long>(nby - 1, t / a.slope);
-        if (by_hi < by_lo) continue;
-        a.t = (int)t;
-        a.by_lo = (int)by_lo;
-        a.count = (int)(by_hi - by_lo + 1);
-        const cudaError_t e = fsrk::launch_reuse(a, p->block, p->precision == FSR_FP64_DEBUG, stream);
+    long long waves = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long nby = (ims[i].H + p->block - 1) / p->block;
+        waves = std::max(waves, (long long)a.slope * (nby - 1) + ims[i].nbx);
+    }
+    auto flush = [&](long long t) -> int {
+        if (a.nseg == 0) return FSR_OK;
+        const cudaError_t e = fsrk::launch_reuse(a, p->block, p->precision == FSR_FP64_DEBUG, h->sm_count, stream);
+        a.nseg = 0;
+        a.total = 0;
         if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "re-use launch %lld failed: %s", t, cudaGetErrorString(e));
+        return FSR_OK;
+    };
+    for (long long t = 0; t < waves; ++t) {
+        a.t = (int)t;
+        for (int i = 0; i < n; ++i) {
+            // blocks of image i with a*by + bx = t, 0 <= bx < nbx, 0 <= by < nby
+            const int nbx = ims[i].nbx, nby = (ims[i].H + p->block - 1) / p->block;
+            const long long lo_num = t - (nbx - 1);
+            const long long by_lo = lo_num <= 0 ? 0 : (lo_num + a.slope - 1) / a.slope;
+            const long long by_hi = std::min<long long>(nby - 1, t / a.slope);
+            if (by_hi < by_lo) continue;
+            fsrk::ReuseSeg& sg = a.seg[a.nseg++];
+            sg.im = ims[i];
+            sg.by_lo = (int)by_lo;
+            sg.count = (int)(by_hi - by_lo + 1);
+            sg.first = a.total;
+            a.total += sg.count;
+            if (a.nseg == fsrk::kReuseSegs) {
+                const int r = flush(t);
+                if (r != FSR_OK) return r;
+            }
+        }
+        const int r = flush(t);
+        if (r != FSR_OK) return r;
     }
     return ok(h);
+}
+
+int enqueue_reuse(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
+                  const fsr_params* p, float* out, cudaStream_t stream) {
+    const fsrk::ImageArgs im = image_args(img, mask, out, p->seq_out, height, width, pitch, p->iters, p->block);
+    return enqueue_reuse_images(h, 1, &im, p, stream);
 }
 
 int enqueue_single(fsr_handle* h, const float* img, const uint8_t* mask, int height, int width, int pitch,
@@ -330,8 +360,6 @@ int check_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_params*
     if (r != FSR_OK) return r;
     if (p->precision != FSR_FP32 && p->precision != FSR_FP64_DEBUG)
         return fail(h, FSR_ERR_UNSUPPORTED, "the batch form runs FSR_FP32 or FSR_FP64_DEBUG");
-    if (p->reuse > 0.f)
-        return fail(h, FSR_ERR_UNSUPPORTED, "re-use of reconstructed pixels runs in the single-image entry points");
     for (int i = 0; i < n; ++i) {
         r = check_image(h, d[i].img, d[i].mask, d[i].out, d[i].height, d[i].width, d[i].pitch, d[i].iters, true, i);
         if (r != FSR_OK) return r;
@@ -702,6 +730,14 @@ int fsr_reconstruct_batch(fsr_handle* h, int n, const fsr_image_desc* d, const f
     DeviceGuard g;
     cudaError_t e = g.set(h->device);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    if (p->reuse > 0.f) {
+        // re-use form: every image's wavefront chain, the images sharing the launches
+        std::vector<fsrk::ImageArgs> ims((size_t)n);
+        for (int i = 0; i < n; ++i)
+            ims[i] = image_args(d[i].img, d[i].mask, d[i].out, d[i].seq_out, d[i].height, d[i].width, d[i].pitch,
+                                d[i].iters, p->block);
+        return enqueue_reuse_images(h, n, ims.data(), p, static_cast<cudaStream_t>(stream));
+    }
     // the previous batch of this handle must be done with the table
     if ((e = cudaEventSynchronize(h->table_free)) != cudaSuccess)
         return fail(h, FSR_ERR_CUDA, "waiting for the previous batch: %s", cudaGetErrorString(e));
@@ -747,6 +783,9 @@ int fsr_batch_create(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_pa
     *out = nullptr;
     int r = check_batch(h, n, d, p);
     if (r != FSR_OK) return r;
+    if (p->reuse > 0.f)
+        return fail(h, FSR_ERR_UNSUPPORTED, "graph plans run independent blocks (reuse = 0); re-use runs in "
+                                            "fsr_reconstruct and fsr_reconstruct_batch");
     DeviceGuard g;
     cudaError_t e = g.set(h->device);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -796,6 +835,8 @@ int fsr_autotune_batch(fsr_handle* h, int n, const fsr_image_desc* d, const fsr_
     if (!h) return fail(nullptr, FSR_ERR_INVALID_ARG, "handle is NULL");
     int r = check_batch(h, n, d, p);
     if (r != FSR_OK) return r;
+    if (p->reuse > 0.f)
+        return fail(h, FSR_ERR_UNSUPPORTED, "the schedule autotuner times independent blocks (reuse = 0)");
     DeviceGuard g;
     cudaError_t e = g.set(h->device);
     if (e != cudaSuccess) return fail(h, FSR_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));

@@ -60,7 +60,7 @@ cudaError_t launch_batch_conj(const BatchArgs& a, int fp64, int sm_count, cudaSt
 // Re-use of reconstructed pixels: one wavefront launch (FP32 with
 // kWarpsFp32 warps per CTA, FP64 with 4), any B of S = 32.
 cudaError_t configure_reuse();
-cudaError_t launch_reuse(const ReuseLaunch& a, int B, int fp64, cudaStream_t stream);
+cudaError_t launch_reuse(const ReuseLaunch& a, int B, int fp64, int sm_count, cudaStream_t stream);
 
 // Warps-per-CTA values instantiated for (precision, B): FP32 has 8 for every
 // B and also 12 and 16 for B = 4; FP64 has 4.

@@ -198,11 +198,13 @@ def _geometry(img, mask, out):
         raise ValueError("img, mask and out must be 2-D tensors of one shape")
     if img.dtype != torch.float32 or out.dtype != torch.float32 or mask.dtype != torch.uint8:
         raise ValueError("img/out must be float32 and mask uint8")
-    pitch = img.stride(0)
+    H, W = img.shape
+    # the stride of a dimension of size 1 is arbitrary in torch and never used
+    pitch = img.stride(0) if H > 1 else W
     for t in (img, mask, out):
-        if t.stride(1) != 1 or t.stride(0) != pitch:
+        if (W > 1 and t.stride(1) != 1) or (H > 1 and t.stride(0) != pitch):
             raise ValueError("img, mask and out must share one row pitch with unit column stride")
-    return img.shape[0], img.shape[1], pitch
+    return H, W, pitch
 
 
 def fsr_reconstruct(handle, img, mask, params: fsr_params, out, stream=None) -> None:

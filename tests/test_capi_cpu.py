@@ -84,3 +84,19 @@ def test_static_batch_rejects_bad_parameters_before_any_device_work(lib):
         assert buf.value
     assert lib.fsr_reconstruct_batch_static(0, d, ctypes.byref(fsr.make_params()), None, buf,
                                             len(buf)) == fsr.FSR_ERR_INVALID_ARG
+
+
+def test_binding_geometry_ignores_strides_of_size_one_dimensions():
+    """The row pitch the binding passes is the image's; a dimension of size
+    1 has an arbitrary stride in torch and must not be compared."""
+    torch = pytest.importorskip("torch")
+    from paper_2202_13926_gb300 import fsr
+    one = torch.zeros((1, 1), dtype=torch.float32)
+    odd = torch.zeros((2, 2), dtype=torch.float32)[:1, :1]   # stride (2, 1)
+    m = torch.zeros((1, 1), dtype=torch.uint8)
+    assert fsr._geometry(one, m, odd) == (1, 1, 1)
+    row = torch.zeros((1, 7), dtype=torch.float32)
+    assert fsr._geometry(row, torch.zeros((1, 7), dtype=torch.uint8), torch.zeros((3, 7))[:1]) == (1, 7, 7)
+    img = torch.zeros((4, 5), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        fsr._geometry(img, torch.zeros((4, 5), dtype=torch.uint8), torch.zeros((4, 6))[:, :5])

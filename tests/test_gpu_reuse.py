@@ -165,9 +165,51 @@ def test_host_entry_point_and_rejections(fsr_mod, handle):
             handle.reconstruct(ti, tm, **kw)
         assert e.value.code == code, kw
     to = torch.empty_like(ti)
-    with pytest.raises(fsr.FsrError) as e:
-        fsr.fsr_reconstruct_batch(handle.ptr, [fsr.image_desc(ti, tm, to, 10)], fsr.make_params(reuse=0.5))
+    with pytest.raises(fsr.FsrError) as e:   # graph plans run independent blocks
+        fsr.fsr_batch_create(handle.ptr, [fsr.image_desc(ti, tm, to, 10)], fsr.make_params(reuse=0.5))
     assert e.value.code == fsr.FSR_ERR_UNSUPPORTED
+
+
+def _batch_vs_single(fsr_mod, handle, shapes, precision, seed0):
+    """Every image of a re-use batch against its single-image call, bit for
+    bit (outputs and selection sequences)."""
+    fsr = fsr_mod
+    dev = torch.device("cuda:0")
+    imgs, descs, singles = [], [], []
+    for i, (H, W, K) in enumerate(shapes):
+        img = synth.pink_image(H, W, seed=seed0 + i)
+        mask = synth.quarter_mask(H, W, seed=seed0 + 100 + i) if i % 2 else synth.iid_mask(H, W, seed=seed0 + i,
+                                                                                            missing=0.6)
+        ti = torch.from_numpy(np.ascontiguousarray(img)).to(dev)
+        tm = torch.from_numpy(np.ascontiguousarray(mask)).to(dev)
+        n = -(-H // 4) * -(-W // 4)
+        out = torch.full_like(ti, -1.0)
+        seq = torch.full((n * max(K, 1),), -7, dtype=torch.int16, device=dev)
+        imgs.append((ti, tm, out, seq))
+        descs.append(fsr.image_desc(ti, tm, out, K, seq_out=seq))
+        s_seq = torch.full((n * max(K, 1),), -7, dtype=torch.int16, device=dev)
+        s_out = handle.reconstruct(ti, tm, iters=K, precision=precision, seq_out=s_seq, reuse=DELTA)
+        singles.append((s_out, s_seq))
+    fsr.fsr_reconstruct_batch(handle.ptr, descs, fsr.make_params(precision=precision, reuse=DELTA))
+    torch.cuda.synchronize()
+    handle.check_status()
+    for (ti, tm, out, seq), (s_out, s_seq) in zip(imgs, singles):
+        assert torch.equal(out, s_out)
+        assert torch.equal(seq, s_seq)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_equals_single_images(fsr_mod, handle, precision):
+    """Images of different sizes and K share the wavefront launches; each
+    gets exactly its single-image result."""
+    shapes = [(128, 128, 60), (37, 53, 25), (270, 480, 40), (1, 1, 5), (64, 200, 0), (90, 33, 30)]
+    _batch_vs_single(fsr_mod, handle, shapes, precision, seed0=40)
+
+
+def test_batch_of_more_images_than_one_launch_holds(fsr_mod, handle):
+    """52 images: wavefront t takes two launches (48 + 4 images)."""
+    shapes = [(40 + 4 * (i % 3), 36 + 8 * (i % 4), 20 + i % 30) for i in range(52)]
+    _batch_vs_single(fsr_mod, handle, shapes, "fp32", seed0=70)
 
 
 def test_quarter_sampled_frame_fp64(handle):
