@@ -1244,20 +1244,39 @@ struct ReuseSeg {
 };
 constexpr int kReuseSegs = 48;   // images per launch (the launch parameters stay below 4 KB)
 
-struct ReuseLaunch {
+// The parameters of one wavefront launch, with room for NSEG images: a
+// single image launches with NSEG = 1 (about 100 bytes of parameters per
+// launch instead of 3.5 KB).
+template <int NSEG>
+struct ReuseLaunchN {
     MethodArgs mth;
     float delta;            // re-use weight (0 < delta <= 1)
     int t;                  // wavefront
     int slope;              // a = ceil(L / B) + 1
     int nseg, total;        // segments, and the blocks they hold
     unsigned long long* empty;
-    ReuseSeg seg[kReuseSegs];
+    ReuseSeg seg[NSEG];
 };
+using ReuseLaunch = ReuseLaunchN<kReuseSegs>;
 static_assert(sizeof(ReuseLaunch) <= 4096, "re-use launch parameters must fit the 4 KB parameter space");
 
-template <typename T, int B, int WARPS>
+// the first segment of a launch, as a one-image launch
+inline ReuseLaunchN<1> one_image(const ReuseLaunch& a) {
+    ReuseLaunchN<1> b;
+    b.mth = a.mth;
+    b.delta = a.delta;
+    b.t = a.t;
+    b.slope = a.slope;
+    b.nseg = 1;
+    b.total = a.seg[0].count;
+    b.empty = a.empty;
+    b.seg[0] = a.seg[0];
+    return b;
+}
+
+template <typename T, int B, int WARPS, int NSEG>
 __global__ void __launch_bounds__(WARPS * 32, MinBlocks<T, WARPS>::value)
-fsr_reuse_kernel(const __grid_constant__ ReuseLaunch a) {
+fsr_reuse_kernel(const __grid_constant__ ReuseLaunchN<NSEG> a) {
     using T2 = typename Vec2<T>::type;
     using Lay = SmemLayout<T>;
     extern __shared__ __align__(128) unsigned char smem[];
