@@ -1297,15 +1297,23 @@ fsr_reuse_kernel(const __grid_constant__ ReuseLaunchN<NSEG> a) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int j = blockIdx.x * WARPS + warp;
     if (j >= a.total) return;
-    int s = 0;   // the segment (image) of block j
-    while (s + 1 < a.nseg && a.seg[s + 1].first <= j) ++s;
-    const ReuseSeg& sg = a.seg[s];
-    const int by = sg.by_lo + (j - sg.first);
-    const int bx = a.t - a.slope * by;
     TileReq tr;
     tr.maps = nullptr;
-    process_block<T, B, false, true>(sg.im, (long long)by * sg.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0, swf, scs,
-                                     Wd, rowbuf, tr, a.empty, lane, a.delta);
+    if constexpr (NSEG == 1) {
+        // one image: its fields at fixed offsets of the parameter space
+        const int by = a.seg[0].by_lo + j;
+        const int bx = a.t - a.slope * by;
+        process_block<T, B, false, true>(a.seg[0].im, (long long)by * a.seg[0].im.nbx + bx, a.mth.L,
+                                         T(a.mth.gamma), sw0, swf, scs, Wd, rowbuf, tr, a.empty, lane, a.delta);
+    } else {
+        int s = 0;   // the segment (image) of block j
+        while (s + 1 < a.nseg && a.seg[s + 1].first <= j) ++s;
+        const ReuseSeg& sg = a.seg[s];
+        const int by = sg.by_lo + (j - sg.first);
+        const int bx = a.t - a.slope * by;
+        process_block<T, B, false, true>(sg.im, (long long)by * sg.im.nbx + bx, a.mth.L, T(a.mth.gamma), sw0, swf,
+                                         scs, Wd, rowbuf, tr, a.empty, lane, a.delta);
+    }
 }
 
 }  // namespace fsrk
