@@ -219,3 +219,20 @@ def test_quarter_sampled_frame_fp64(handle):
     got, seq = _run(handle, img, mask, precision="fp64", seq=True)
     r = _oracle(img, mask)
     _fp64_check(got, seq, r, 270, 480, 4)
+
+
+def test_multichannel_frame_in_the_reuse_form(fsr_mod, handle):
+    """The planes of a multi-channel frame run their raster orders in one
+    batch (shared wavefront launches); each equals its single-plane call."""
+    dev = torch.device("cuda:0")
+    C, H, W, K = 3, 96, 160, 40
+    planes = np.stack([synth.pink_image(H, W, seed=300 + c) for c in range(C)])
+    mask = synth.quarter_mask(H, W, seed=310)
+    ti = torch.from_numpy(planes).to(dev)
+    tm = torch.from_numpy(np.ascontiguousarray(mask)).to(dev)
+    got = handle.reconstruct_channels(ti, tm, iters=K, reuse=DELTA)
+    torch.cuda.synchronize()
+    for c in range(C):
+        one = handle.reconstruct(ti[c].contiguous(), tm, iters=K, reuse=DELTA)
+        torch.cuda.synchronize()
+        assert torch.equal(got[c], one)
