@@ -190,6 +190,30 @@ def test_invalid_arguments_report_codes(handle):
     assert e.value.code == fsr.FSR_ERR_INVALID_ARG
 
 
+def test_largest_iteration_count(handle):
+    """K = 65535, the largest the C-ABI takes, on one 32 x 32 support (the
+    int16 index buffer and the loop counters at their limit): the FP64 path
+    selects the oracle's first 200 components (up to the tie class), the FP32
+    output stays finite with the known pixels exact, every recorded index is
+    a component, and K = 65536 is rejected."""
+    from paper_2202_13926_gb300 import fsr
+    img = synth.sinusoid_image(4, 4, seed=5)
+    mask = synth.iid_mask(4, 4, seed=6, missing=0.5)
+    K = 65535
+    got64, seq64 = run_gpu(handle, img, mask, iters=K, precision="fp64", seq=True)
+    _, r = run_oracle(img, mask, K=200)
+    n_hard, _ = PA.sequence_mismatches(seq64[:, :200], r["seq"], r["margin"])
+    assert n_hard == 0
+    got, seq = run_gpu(handle, img, mask, iters=K, seq=True)
+    assert np.all(np.isfinite(got))
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    assert seq.min() >= 0 and seq.max() < 1024
+    dev = torch.device("cuda:0")
+    with pytest.raises(fsr.FsrError) as e:
+        handle.reconstruct(torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev), iters=K + 1)
+    assert e.value.code == fsr.FSR_ERR_INVALID_ARG
+
+
 def test_fhd_quarter_full_frame(handle):
     """1920 x 1080 quarter sampling at K = 100 in the bench's launch
     configuration, against the oracle on every block of the frame (the
