@@ -285,8 +285,11 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
 
     // One iteration; dc = false when no running group of the warp is in its
     // DC phase (the split branches then drop out at compile time).
-    auto step = [&](int nu, bool dc) {
-        const bool run = active && nu < Kh;
+    auto step = [&](int nu, bool dc, bool all) {
+        // all: every group of the warp holds an active block with K = Kmax,
+        // so the per-group run conditions drop out at compile time
+        const bool run = all || (active && nu < Kh);
+        const int Kr = all ? Kmax : Kh;
         // a5: block maximum (each group reduces over its own lanes), the
         // lowest row holding it, then its lowest column
         const unsigned Mb = __reduce_max_sync(gmask, run ? __float_as_uint(m_lane) : 0u);
@@ -322,7 +325,7 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
             }
         }
         // a7 (Eq. 12) and the objective of the next iteration (this group only)
-        if (run && nu + 1 < Kh) {
+        if (run && nu + 1 < Kr) {
             if (dc && split && (u | v) == 0) {
                 ar -= cr;
                 ai -= ci;
@@ -352,10 +355,18 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     // the loops run to the largest K of the warp (uniform): a DC loop, then a
     // loop without the split branches (1080p frame: S = 4 0.385 -> 0.365 ms,
     // S = 8 0.776 -> 0.747 ms; S = 16 at 20 warps per SM 1.935 -> 1.922 ms,
-    // at 16 warps and 123 registers 2.07 -> 2.15 ms)
+    // at 16 warps and 123 registers 2.07 -> 2.15 ms), in a form without the
+    // per-group run conditions when every group runs to the same K (S = 16
+    // 1.902 -> 1.848 ms, S = 4 0.369 -> 0.358 ms; S = 8 unchanged, with 32
+    // bytes spilled, so it keeps one form)
     int nu = 0;
-    while (nu < Kmax && __any_sync(FULL, split && active && nu < Kh)) step(nu++, true);
-    for (; nu < Kmax; ++nu) step(nu, false);
+    while (nu < Kmax && __any_sync(FULL, split && active && nu < Kh)) step(nu++, true, false);
+    if constexpr (SZ != 8) {
+        if (__all_sync(FULL, active && Kh == Kmax)) {
+            for (; nu < Kmax; ++nu) step(nu, false, true);
+        }
+    }
+    for (; nu < Kmax; ++nu) step(nu, false, false);
 
 
     // ---- a9: write-back of the B x B target ----
