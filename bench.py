@@ -544,7 +544,7 @@ def run_case(args):
     d_img, d_mask = torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)
     d_out = torch.empty_like(d_img)
     params = fsr.make_params(block=B, border=(args.support - B) // 2, iters=args.iters, rho=RHO, gamma=GAMMA,
-                             precision=args.precision, update=args.update)
+                             precision=args.precision, update=args.update, reuse=args.reuse)
     ms = []
     with fsr.Handle(0) as h:
         for _ in range(args.repeat):
@@ -557,7 +557,8 @@ def run_case(args):
             ms.append(a.elapsed_time(b))
         h.check_status()
     print(json.dumps({"case": True, "support": args.support, "block": B, "iters": args.iters,
-                      "precision": args.precision, "update": args.update, "ms": ms}), flush=True)
+                      "precision": args.precision, "update": args.update, "reuse": args.reuse, "ms": ms}),
+          flush=True)
 
 
 def main():
@@ -580,6 +581,8 @@ def main():
     ap.add_argument("--precision", default="fp32", help="--case: fp32, fp64, tc_bf16x3 or tc_tf32")
     ap.add_argument("--update", default="single", help="--case: single or conj_pair")
     ap.add_argument("--repeat", type=int, default=3, help="--case: launches")
+    ap.add_argument("--reuse", type=float, default=0.0,
+                    help="--case: re-use weight delta (0 = independent blocks; > 0 = one launch per wavefront)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _dist_env()
