@@ -157,7 +157,6 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
     constexpr int WS = G::WS, TS = G::TS, WFS = G::WFS;
     constexpr int PT = (B * B + SZ - 1) / SZ;   // target pixels per lane
     const int t = lane & (SZ - 1), gb = lane & ~(SZ - 1);
-    const unsigned gmask = G::LOW << gb;
     int by = 0, bx = 0;
     if (valid) {
         by = (int)(blk / im.nbx);
@@ -292,14 +291,10 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
         const int Kr = all ? Kmax : Kh;
         // a5: block maximum (each group reduces over its own lanes), the
         // lowest row holding it, then its lowest column
-        // (a warp reduction with a group mask runs once per group: at S = 4
-        // and 8, with 8 and 4 groups per warp, a butterfly over the group's
-        // lanes is faster (1080p: S = 4 0.366 -> 0.270 ms, S = 8 0.718 ->
-        // 0.705 ms); at S = 16 the two half-warp reductions win (2.11
-        // against 2.13 ms))
-        unsigned Mb;
-        if constexpr (SZ <= 8) Mb = group_umax<SZ>(run ? __float_as_uint(m_lane) : 0u);
-        else Mb = __reduce_max_sync(gmask, run ? __float_as_uint(m_lane) : 0u);
+        // (a butterfly over the group's lanes: a warp reduction with the
+        // group's lane mask runs once per group; 1080p: S = 4 0.366 -> 0.270
+        // ms, S = 8 0.718 -> 0.705 ms, S = 16 1.842 -> 1.798 ms)
+        const unsigned Mb = group_umax<SZ>(run ? __float_as_uint(m_lane) : 0u);
         const unsigned ub = (__ballot_sync(FULL, run && __float_as_uint(m_lane) == Mb) >> gb) & G::LOW;
         const int u = ub ? __ffs(ub) - 1 : 0;
         __syncwarp();   // the previous pick's reads of the published row are done
