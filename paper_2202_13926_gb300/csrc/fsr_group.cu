@@ -47,7 +47,12 @@ struct Grp {
     static_assert(SZ >= 16 || REGION % 16 == SZ, "regions of the groups of a half-warp on distinct bank pairs");
     static constexpr size_t w0_off = 0;
     static constexpr size_t wf_off = w0_off + 4 * SZ * SZ;
-    static constexpr size_t cs_off = wf_off + 4 * SZ * WFS;
+    // w_f again with one copy per group of a warp side by side in 32-word
+    // rows: group g reads its copy at words 32 u + S g + t, on banks no other
+    // group of the warp touches, whatever row u it picked (1080p: S = 8
+    // 0.702 -> 0.683 ms, S = 16 1.797 -> 1.776 ms)
+    static constexpr size_t wfg_off = wf_off + 4 * SZ * WFS;
+    static constexpr size_t cs_off = wfg_off + 4 * SZ * 32;
     static constexpr size_t warp0_off = (cs_off + 8 * SZ + 127) & ~(size_t)127;
     static constexpr size_t per_warp = (size_t)8 * REGION * BPW;
     static constexpr size_t bytes(int warps) { return warp0_off + per_warp * (size_t)warps; }
@@ -151,7 +156,8 @@ __device__ __forceinline__ float split_objective_row(const float (&zr)[SZ], cons
 template <int SZ, int B>
 __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, bool valid, int Kmax, int L,
                                             float gamma, const float* __restrict__ sw0,
-                                            const float* __restrict__ swf, const float2* __restrict__ scs,
+                                            const float* __restrict__ swf, const float* __restrict__ swfg,
+                                            const float2* __restrict__ scs,
                                             float2* Wd, float2* rowbuf, unsigned long long* empty, int lane) {
     using G = Grp<SZ>;
     constexpr int WS = G::WS, TS = G::TS, WFS = G::WFS;
@@ -310,7 +316,7 @@ __device__ __forceinline__ void group_block(const ImageArgs& im, long long blk, 
             const float2 w = Wd[u * WS + t];
             split_value(ar, ai, w.x, w.y, qv.x, qv.y, rr, ri);
         }
-        const float o = objective<float>(rr, ri, swf[u * WFS + t]);
+        const float o = objective<float>(rr, ri, swfg[u * 32 + gb + t]);
         const unsigned vbits = (__ballot_sync(FULL, run && __float_as_uint(o) == Mb) >> gb) & G::LOW;
         const int v = vbits ? __ffs(vbits) - 1 : 0;
         const float Rr = __shfl_sync(FULL, rr, gb + v);
@@ -403,6 +409,7 @@ __global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_ke
     float* sw0 = reinterpret_cast<float*>(smem + G::w0_off);
     float* swf = reinterpret_cast<float*>(smem + G::wf_off);
     float2* scs = reinterpret_cast<float2*>(smem + G::cs_off);
+    float* swfg = reinterpret_cast<float*>(smem + G::wfg_off);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int grp = lane / SZ;
@@ -423,6 +430,8 @@ __global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_ke
             wfv = b * b;
         }
         swf[m * G::WFS + n] = wfv;
+#pragma unroll
+        for (int g = 0; g < G::BPW; ++g) swfg[m * 32 + g * SZ + n] = wfv;
     }
     for (int i = threadIdx.x; i < SZ; i += blockDim.x)
         scs[i] = make_float2(float(cos_2pi32(i * (32 / SZ))), float(sin_2pi32(i * (32 / SZ))));
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(WARPS * 32, group_min_ctas<SZ>()) fsr_group_ke
             int Kmax = valid ? im.K : 0;
 #pragma unroll
             for (int s = 16; s >= SZ; s >>= 1) Kmax = max(Kmax, __shfl_xor_sync(FULL, Kmax, s));
-            group_block<SZ, B>(im, blk, valid, Kmax, a.mth.L, gamma, sw0, swf, scs, Wd, rowbuf, a.empty, lane);
+            group_block<SZ, B>(im, blk, valid, Kmax, a.mth.L, gamma, sw0, swf, swfg, scs, Wd, rowbuf, a.empty, lane);
         }
     }
 }
