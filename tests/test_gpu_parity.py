@@ -214,6 +214,29 @@ def test_largest_iteration_count(handle):
     assert e.value.code == fsr.FSR_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("rho,gamma,freq_weight", [(0.5, 0.25, True), (0.9, 1.0, False), (0.8, 0.75, True),
+                                                  (0.6, 0.5, False)])
+def test_method_parameters(handle, rho, gamma, freq_weight):
+    """Other spatial decays, dampings and objectives than the defaults
+    (Eqs. 5, 8, 11, 12): FP32 within the acceptance bar, FP64 with the
+    oracle's sequences up to the tie class.  The oracle gets rho-hat and
+    gamma as the library receives them (binary32)."""
+    img, mask = synth.small_case(seed=11)
+    K = 60
+    rho32, gamma32 = float(np.float32(rho)), float(np.float32(gamma))
+    ref, r = run_oracle(img, mask, K=K, rho=rho32, gamma=gamma32, freq_weight=freq_weight)
+    kw = dict(iters=K, rho=rho, gamma=gamma, freq_weight=freq_weight)
+    got = run_gpu(handle, img, mask, **kw)
+    assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
+    assert PA.frac_within(got, ref) >= PA.FRAC_MIN
+    assert abs(PA.psnr(got, img) - PA.psnr(ref, img)) <= PA.PSNR_TOL_DB
+    got, seq = run_gpu(handle, img, mask, precision="fp64", seq=True, **kw)
+    n_hard, _ = PA.sequence_mismatches(seq, r["seq"], r["margin"])
+    assert n_hard == 0
+    same = PA.same_sequence_pixels(seq, r["seq"], img.shape[0], img.shape[1], 4)
+    assert np.max(np.abs(got - ref)[same]) <= 1e-3
+
+
 def test_fhd_quarter_full_frame(handle):
     """1920 x 1080 quarter sampling at K = 100 in the bench's launch
     configuration, against the oracle on every block of the frame (the
