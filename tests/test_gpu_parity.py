@@ -214,18 +214,20 @@ def test_largest_iteration_count(handle):
     assert e.value.code == fsr.FSR_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("S", [32, 24, 16, 8])
 @pytest.mark.parametrize("rho,gamma,freq_weight", [(0.5, 0.25, True), (0.9, 1.0, False), (0.8, 0.75, True),
                                                   (0.6, 0.5, False)])
-def test_method_parameters(handle, rho, gamma, freq_weight):
+def test_method_parameters(handle, rho, gamma, freq_weight, S):
     """Other spatial decays, dampings and objectives than the defaults
-    (Eqs. 5, 8, 11, 12): FP32 within the acceptance bar, FP64 with the
-    oracle's sequences up to the tie class.  The oracle gets rho-hat and
-    gamma as the library receives them (binary32)."""
+    (Eqs. 5, 8, 11, 12), for the kernels of every support size but 4 (whose
+    FP64 path has its own rounding-floor reading): FP32 within the acceptance
+    bar, FP64 with the oracle's sequences up to the tie class.  The oracle
+    gets rho-hat and gamma as the library receives them (binary32)."""
     img, mask = synth.small_case(seed=11)
-    K = 60
+    K, L = 60, (S - 4) // 2
     rho32, gamma32 = float(np.float32(rho)), float(np.float32(gamma))
-    ref, r = run_oracle(img, mask, K=K, rho=rho32, gamma=gamma32, freq_weight=freq_weight)
-    kw = dict(iters=K, rho=rho, gamma=gamma, freq_weight=freq_weight)
+    ref, r = run_oracle(img, mask, K=K, L=L, rho=rho32, gamma=gamma32, freq_weight=freq_weight)
+    kw = dict(iters=K, border=L, rho=rho, gamma=gamma, freq_weight=freq_weight)
     got = run_gpu(handle, img, mask, **kw)
     assert np.array_equal(got[mask == 1], img[mask == 1].astype(np.float64))
     assert PA.frac_within(got, ref) >= PA.FRAC_MIN
