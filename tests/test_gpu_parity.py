@@ -141,18 +141,24 @@ def test_nan_at_unknown_pixels_is_ignored(handle):
     assert np.array_equal(a, b)
 
 
-def test_row_pitch_larger_than_width(handle):
+@pytest.mark.parametrize("kw", [dict(), dict(border=6), dict(border=10), dict(border=2), dict(border=0),
+                                dict(precision="fp64", border=6), dict(reuse=0.5)],
+                         ids=["S32", "S16", "S24", "S8", "S4", "S16fp64", "reuse"])
+def test_row_pitch_larger_than_width(handle, kw):
+    """Images inside wider rows (pitch > width, not a multiple of 16: the
+    plain-load path) give the dense image's result bit for bit and leave the
+    pixels beyond the width untouched, for every kernel family."""
     from paper_2202_13926_gb300 import fsr
     img, mask = synth.small_case(seed=6)
     H, W = img.shape
-    P = W + 24
+    P = W + 23
     dev = torch.device("cuda:0")
     bi = torch.full((H, P), -1.0, device=dev); bm = torch.zeros((H, P), dtype=torch.uint8, device=dev)
     bo = torch.full((H, P), -5.0, device=dev)
     bi[:, :W] = torch.from_numpy(img).to(dev); bm[:, :W] = torch.from_numpy(mask).to(dev)
-    fsr.fsr_reconstruct(handle.ptr, bi[:, :W], bm[:, :W], fsr.make_params(iters=30), bo[:, :W])
+    fsr.fsr_reconstruct(handle.ptr, bi[:, :W], bm[:, :W], fsr.make_params(iters=30, **kw), bo[:, :W])
     torch.cuda.synchronize()
-    dense = run_gpu(handle, img, mask, iters=30)
+    dense = run_gpu(handle, img, mask, iters=30, **kw)
     assert np.array_equal(bo[:, :W].cpu().numpy().astype(np.float64), dense)
     assert torch.all(bo[:, W:] == -5.0)
 
