@@ -236,3 +236,25 @@ def test_multichannel_frame_in_the_reuse_form(fsr_mod, handle):
         one = handle.reconstruct(ti[c].contiguous(), tm, iters=K, reuse=DELTA)
         torch.cuda.synchronize()
         assert torch.equal(got[c], one)
+
+
+def test_two_streams_in_flight(fsr_mod, handle):
+    """Two re-use frames enqueued on two streams of one handle without a
+    synchronisation in between (two chains of programmatic dependent
+    launches at once): each equals its result alone."""
+    fsr = fsr_mod
+    dev = torch.device("cuda:0")
+    frames = [synth.fhd_quarter_case(seed=60 + i, H=135, W=240) for i in range(2)]
+    alone = []
+    for img, mask in frames:
+        alone.append(_run(handle, img, mask, K=40))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    bufs = [(torch.from_numpy(img).to(dev), torch.from_numpy(mask).to(dev)) for img, mask in frames]
+    outs = [torch.empty_like(ti) for ti, _ in bufs]
+    torch.cuda.synchronize()   # inputs on the device; from here on nothing waits
+    for (ti, tm), out, st in zip(bufs, outs, streams):
+        fsr.fsr_reconstruct(handle.ptr, ti, tm, fsr.make_params(iters=40, reuse=DELTA), out, st)
+    torch.cuda.synchronize()
+    handle.check_status()
+    for out, ref in zip(outs, alone):
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), ref)
