@@ -703,76 +703,103 @@ def main():
     }
 
     if world == 1 and not args.no_k_sweep:
-        line["k_sweep"] = _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torch)
-        line["param_sweep"] = _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch)
-        line["s_sweep"] = _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
-        line["ablation_update"] = _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch)
-        line["reuse_reconstructed"] = _measure_reuse(fsr, handle, img, mask, d_img, d_mask, d_out, stream, flush,
-                                                     torch)
+        _leg(line, "k_sweep", lambda: _measure_k_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, dev, torch))
+        _leg(line, "param_sweep", lambda: _measure_param_sweep(fsr, handle, d_img, d_mask, d_out, stream, torch))
+        _leg(line, "s_sweep", lambda: _measure_s_sweep(fsr, handle, d_img, d_mask, d_out, stream, flush, torch))
+        _leg(line, "ablation_update",
+             lambda: _measure_conj_pair(fsr, handle, d_img, d_mask, d_out, stream, flush, torch))
+        _leg(line, "reuse_reconstructed",
+             lambda: _measure_reuse(fsr, handle, img, mask, d_img, d_mask, d_out, stream, flush, torch))
     if world == 1 and not args.no_batch:
-        line["batch"] = _measure_batch(fsr, handle, dev, torch)
+        _leg(line, "batch", lambda: _measure_batch(fsr, handle, dev, torch))
     if world == 1 and args.serve_seconds > 0:
-        line["frame_stream"] = _measure_stream(fsr, handle, torch, img, mask)
-        line["frame_stream_S16"] = _measure_stream(fsr, handle, torch, img, mask, support=16)
-    if world == 1 and args.serve_seconds > 0:
-        line["serving"] = _measure_serving(fsr, handle, torch, args.serve_seconds)
+        _leg(line, "frame_stream", lambda: _measure_stream(fsr, handle, torch, img, mask))
+        _leg(line, "frame_stream_S16", lambda: _measure_stream(fsr, handle, torch, img, mask, support=16))
+        _leg(line, "serving", lambda: _measure_serving(fsr, handle, torch, args.serve_seconds))
 
     if world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        threads = os.cpu_count() or 1
-        rows = _calibrated_rows(img, mask, threads, target_s=10.0)
-        res, ids, t = _oracle_sample(img, mask, rows, threads)
-        nbx = W // B
-        got = np.stack([out[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
-        truth = np.stack([img[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
-        ref = res["target"]
-        d = np.abs(got.astype(np.float64) - ref)
-
-        def psnr(x):
-            e = np.mean((np.asarray(x, np.float64) - truth) ** 2)
-            return 10 * np.log10(255.0 ** 2 / e)
-        frac = float(np.mean(d <= 0.5))
-        dpsnr = abs(psnr(got) - psnr(ref))
-        # one core on every 16th block row (the frame time is extrapolated)
-        nby = -(-H // B)
-        rows1 = list(range(0, nby, 16))
-        _, ids1, t1 = _oracle_sample(img, mask, rows1, 1)
-        line["cpu_baseline"] = {
-            "value": len(ids) * B * B / 1e6 / t, "unit": "MP/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(rows)} of {nby} block rows of the frame ({len(ids)} blocks), FP64 C oracle, OpenMP over blocks",
-            "single_core": {"value": len(ids1) * B * B / 1e6 / t1, "unit": "MP/s", "cores": 1,
-                            "sample": f"{len(rows1)} of {nby} block rows (every 16th), one thread",
-                            "frame_s_extrapolated": t1 * nby / len(rows1)}}
-        im = res["im_target"]
-        line["parity"] = {"frac_within_0.5": frac, "max_abs_diff": float(d.max()),
-                          "psnr_gpu_db": psnr(got), "psnr_oracle_db": psnr(ref),
-                          "dpsnr_db": dpsnr, "pass": bool(frac >= 0.999 and dpsnr <= 0.01),
-                          "blocks_checked": int(len(ids)),
-                          "oracle_max_abs_im_g": float(np.nanmax(np.abs(im))),
-                          "im_g_note": "Im g at unknown pixels (diagnostic of the complex model; the output is Re g)"}
-        # precision study: forward and inverse transforms on tensor cores, same sample
-        study = {}
-        for mode in ("fp32", "tc_bf16x3", "tc_tf32"):
-            pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, precision=mode)
-            for _ in range(2):
-                fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
-            ta = torch.cuda.Event(enable_timing=True)
-            tb = torch.cuda.Event(enable_timing=True)
-            ta.record(stream)
-            for _ in range(5):
-                fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
-            tb.record(stream)
-            torch.cuda.synchronize(dev)
-            o = d_out.cpu().numpy()
-            g = np.stack([o[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
-            dd = np.abs(g.astype(np.float64) - ref)
-            study[mode] = {"ms_per_frame": ta.elapsed_time(tb) / 5, "psnr_db": psnr(g),
-                           "dpsnr_vs_oracle_db": psnr(g) - psnr(ref), "max_abs_vs_oracle": float(dd.max()),
-                           "frac_within_0.5": float(np.mean(dd <= 0.5))}
-        line["precision_study"] = study
+        _leg(line, None, lambda: _cpu_and_precision_legs(fsr, handle, img, mask, out, d_img, d_mask, d_out,
+                                                         stream, dev, torch))
     print(json.dumps(line), flush=True)
     handle.close()
+
+
+def _leg(line, key, fn):
+    """One optional measurement of the JSON line: a failure is recorded under
+    its key (or under "errors") instead of ending the run, so the headline
+    figures are printed in any case."""
+    try:
+        r = fn()
+        if key is None:
+            line.update(r)
+        else:
+            line[key] = r
+    except Exception as e:
+        msg = f"{type(e).__name__}: {e}"[:300]
+        if key is None:
+            line.setdefault("errors", []).append(msg)
+        else:
+            line[key] = {"error": msg}
+
+
+def _cpu_and_precision_legs(fsr, handle, img, mask, out, d_img, d_mask, d_out, stream, dev, torch):
+    """The oracle on the host cores (cpu_baseline), the sampled parity of the
+    timed frame against it, and the precision study on the same sample."""
+    line = {}
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    rows = _calibrated_rows(img, mask, threads, target_s=10.0)
+    res, ids, t = _oracle_sample(img, mask, rows, threads)
+    nbx = W // B
+    got = np.stack([out[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+    truth = np.stack([img[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+    ref = res["target"]
+    d = np.abs(got.astype(np.float64) - ref)
+
+    def psnr(x):
+        e = np.mean((np.asarray(x, np.float64) - truth) ** 2)
+        return 10 * np.log10(255.0 ** 2 / e)
+    frac = float(np.mean(d <= 0.5))
+    dpsnr = abs(psnr(got) - psnr(ref))
+    # one core on every 16th block row (the frame time is extrapolated)
+    nby = -(-H // B)
+    rows1 = list(range(0, nby, 16))
+    _, ids1, t1 = _oracle_sample(img, mask, rows1, 1)
+    line["cpu_baseline"] = {
+        "value": len(ids) * B * B / 1e6 / t, "unit": "MP/s", "cores": threads, "kind": "oracle",
+        "sample": f"{len(rows)} of {nby} block rows of the frame ({len(ids)} blocks), FP64 C oracle, OpenMP over blocks",
+        "single_core": {"value": len(ids1) * B * B / 1e6 / t1, "unit": "MP/s", "cores": 1,
+                        "sample": f"{len(rows1)} of {nby} block rows (every 16th), one thread",
+                        "frame_s_extrapolated": t1 * nby / len(rows1)}}
+    im = res["im_target"]
+    line["parity"] = {"frac_within_0.5": frac, "max_abs_diff": float(d.max()),
+                      "psnr_gpu_db": psnr(got), "psnr_oracle_db": psnr(ref),
+                      "dpsnr_db": dpsnr, "pass": bool(frac >= 0.999 and dpsnr <= 0.01),
+                      "blocks_checked": int(len(ids)),
+                      "oracle_max_abs_im_g": float(np.nanmax(np.abs(im))),
+                      "im_g_note": "Im g at unknown pixels (diagnostic of the complex model; the output is Re g)"}
+    # precision study: forward and inverse transforms on tensor cores, same sample
+    study = {}
+    for mode in ("fp32", "tc_bf16x3", "tc_tf32"):
+        pm = fsr.make_params(block=B, border=L, iters=K_ITERS, rho=RHO, gamma=GAMMA, precision=mode)
+        for _ in range(2):
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        ta = torch.cuda.Event(enable_timing=True)
+        tb = torch.cuda.Event(enable_timing=True)
+        ta.record(stream)
+        for _ in range(5):
+            fsr.fsr_reconstruct(handle.ptr, d_img, d_mask, pm, d_out, stream)
+        tb.record(stream)
+        torch.cuda.synchronize(dev)
+        o = d_out.cpu().numpy()
+        g = np.stack([o[(b // nbx) * B:(b // nbx + 1) * B, (b % nbx) * B:(b % nbx + 1) * B] for b in ids])
+        dd = np.abs(g.astype(np.float64) - ref)
+        study[mode] = {"ms_per_frame": ta.elapsed_time(tb) / 5, "psnr_db": psnr(g),
+                       "dpsnr_vs_oracle_db": psnr(g) - psnr(ref), "max_abs_vs_oracle": float(dd.max()),
+                       "frac_within_0.5": float(np.mean(dd <= 0.5))}
+    line["precision_study"] = study
+    return line
 
 
 if __name__ == "__main__":
